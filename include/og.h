@@ -1,0 +1,223 @@
+/*
+ * og.h -- C ABI of the GB300 short-range gravity library (libog.so).
+ *
+ * The library computes the short-range part of a TreePM gravity force in a
+ * periodic box, i.e. the Barnes-Hut tree walk the paper ports to GPUs
+ * (Sec. 2: a tree walk per active particle; Sec. 3.1: Barnes-Hut for the
+ * short-range force, long-range PM on the host).  The steps are
+ *
+ *   og_keys_sort          63-bit Peano-Hilbert keys + stable radix sort
+ *   og_tree_build         octree with monopole moments, level by level
+ *   og_shortrange_accel   warp-coherent Barnes-Hut walk (FP32 + Kahan, or FP64)
+ *   og_shortrange_adjoint gradient of L = sum_i w_i . a_i with frozen decisions
+ *
+ * Physics conventions (G = 1, attractive, code units):
+ *   a_i = -sum_s m_s K_h(r) f(r) d,  d = x_i - x_s (periodic minimum image),
+ *   f(r) = erfc(r / 2 r_s) + (r / (sqrt(pi) r_s)) exp(-r^2 / 4 r_s^2),
+ *   contributions only for r < rcut = rcut_factor * r_s (default 4.5),
+ *   K_h(r) = 1/r^3 for r >= h, the cubic-spline softened kernel inside,
+ *   h = 2.8 eps, pairs use max(h_i, h_j), node terms max(h_i, hmax_node).
+ * Opening rule for target i and node n (side s, geometric centre c, COM X):
+ *   discard if the node cube is farther than rcut from x_i;
+ *   accept (one monopole term) if s^2 < theta^2 |x_i - X|^2, x_i is outside
+ *   the cube enlarged 1.2x and the whole cube lies within rcut;
+ *   otherwise open (a leaf gives particle-particle terms, self excluded).
+ *
+ * Memory and ownership.  The caller owns every buffer.  Unless stated
+ * otherwise, pointers are DEVICE pointers on the current CUDA device; the
+ * og_params and og_tree structs are HOST structs.  The library never
+ * allocates or frees device memory and never synchronises, except in
+ * og_poll_status / og_tree_node_count.  Every call is asynchronous on the
+ * given stream.  Workspaces are sized by the *_ws_bytes / og_tree_bytes
+ * helpers and must be 256-byte aligned.
+ *
+ * Errors.  Host-side argument errors are returned immediately.  Errors found
+ * on the device (non-finite positions, node capacity exceeded, walk iteration
+ * cap or stack overflow, corrupt links) are recorded in a status word at the
+ * start of the workspace / tree buffer and returned by og_poll_status.  No
+ * C++ exception crosses this interface.
+ */
+#ifndef OG_H
+#define OG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t, passed as an opaque pointer (NULL = the legacy stream). */
+typedef void* og_stream;
+
+typedef enum og_status {
+  OG_OK = 0,
+  OG_EINVAL = 1,    /* bad argument (host check), or non-finite input found on device */
+  OG_ENOSPACE = 2,  /* workspace or tree buffer too small (host), node capacity exceeded (device) */
+  OG_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+  OG_EWALK = 4,     /* walk iteration cap hit or traversal stack overflow (device) */
+  OG_ETREE = 5,     /* tree missing, not built, or with out-of-range links (device) */
+  OG_ENOTIMPL = 6   /* option not implemented */
+} og_status;
+
+typedef enum og_precision {
+  OG_FP32_KAHAN = 0, /* FP32 interactions, compensated per-particle sums, output float[n][3] */
+  OG_FP64 = 1        /* FP64 throughout, output double[n][3] */
+} og_precision;
+
+/* Tunables; the paper fixes none of them.  og_params_default() fills:
+ * leaf_size 8, rcut_factor 4.5, node_capacity 0 (= 2n + 1024),
+ * max_walk_iters 0 (= 2^24 node visits per 32-particle group). */
+typedef struct og_params {
+  int32_t leaf_size;       /* B: a node with more than B particles is split (1..32) */
+  int32_t reserved0;
+  double rcut_factor;      /* rcut = rcut_factor * r_s */
+  int64_t node_capacity;   /* nodes reserved in the tree buffer */
+  int64_t max_walk_iters;  /* node-visit cap per group; exceeding it sets OG_EWALK */
+} og_params;
+
+void og_params_default(og_params* p);
+
+/* Host header of a tree that lives in a caller-owned device buffer.  Filled
+ * by og_tree_build; the fields are read-only for the caller.  The buffer
+ * must stay alive and unmodified while the tree is used. */
+typedef struct og_tree {
+  int64_t n;               /* particles */
+  int64_t n_groups;        /* ceil(n / 32): walk groups of Hilbert-consecutive particles */
+  int64_t node_capacity;
+  double box;              /* periodic box side L */
+  double rcut_factor;
+  int32_t leaf_size;
+  int32_t built;           /* 1 after a successful og_tree_build launch */
+  void* mem;               /* device buffer (starts with the status block) */
+  size_t mem_bytes;
+  int64_t max_walk_iters;
+} og_tree;
+
+/* Bytes of workspace og_keys_sort needs for n particles. */
+size_t og_keys_sort_ws_bytes(int64_t n);
+
+/* Bytes of tree buffer for n particles (p may be NULL for defaults). */
+size_t og_tree_bytes(int64_t n, const og_params* p);
+
+/* Bytes of workspace for og_shortrange_accel / og_shortrange_adjoint. */
+size_t og_accel_ws_bytes(const og_tree* t, og_precision prec);
+size_t og_adjoint_ws_bytes(const og_tree* t, int recompute_lists);
+
+/*
+ * og_keys_sort -- Peano-Hilbert keys and their stable sort.
+ *
+ * The paper builds its tree on the host and offloads it every step (Sec. 2.1,
+ * Appendix A); Gadget-family codes order particles along a Peano-Hilbert
+ * curve (Sec. 2: the infrastructure inherited from Gadget3).  Here:
+ *   w = x - L floor(x / L)            (each axis, FP64, rounded once per op)
+ *   q = clamp(floor((w / L) 2^21), 0, 2^21 - 1)
+ *   key = 63-bit Hilbert index of (q0, q1, q2) (Skilling's transpose form,
+ *         axis 0 most significant within each 3-bit digit)
+ * then (key, index) pairs are sorted ascending, ties by original index.
+ *
+ * pos          device, double[n][3], any real values (wrapped periodically)
+ * n            1 <= n <= 2^31 - 1
+ * box          L > 0
+ * keys_sorted  device out, uint64[n]: keys in ascending order
+ * order        device out, int32[n]: order[k] = original index of the k-th key
+ * ws, ws_bytes device workspace of at least og_keys_sort_ws_bytes(n)
+ * Non-finite positions set OG_EINVAL in the workspace status word.
+ */
+og_status og_keys_sort(const double* pos, int64_t n, double box, uint64_t* keys_sorted, int32_t* order,
+                       void* ws, size_t ws_bytes, og_stream stream);
+
+/*
+ * og_tree_build -- octree with monopole moments over the sorted particles.
+ *
+ * A node is a maximal run of sorted keys that share their top 3*level bits
+ * (the cell at that level); a node with more than leaf_size particles below
+ * level 21 is split into its non-empty octants.  Per node: member range,
+ * mass M = sum m (FP64), centre of mass sum(m x)/M (FP64), geometric centre
+ * and side L / 2^level, largest member softening length.  Built top-down one
+ * level per launch (children by binary search on the keys) and reduced
+ * bottom-up one level per launch.  Particles are copied into Hilbert order.
+ *
+ * keys_sorted, order  outputs of og_keys_sort for the same pos / n / box
+ * pos          device, double[n][3] (original order)
+ * mass         device, double[n] (original order), > 0
+ * eps          device, double[n] softening lengths (original order), or NULL
+ *              to use eps_scalar for every particle; eps > 0
+ * p            tunables (NULL = defaults); tree_mem/tree_bytes: device buffer
+ *              of at least og_tree_bytes(n, p)
+ * tree_out     host struct filled on success
+ * Capacity overflow sets OG_ENOSPACE in the tree status word.
+ */
+og_status og_tree_build(const uint64_t* keys_sorted, const int32_t* order, const double* pos, const double* mass,
+                        const double* eps, double eps_scalar, int64_t n, double box, const og_params* p,
+                        void* tree_mem, size_t tree_bytes, og_tree* tree_out, og_stream stream);
+
+/*
+ * og_shortrange_accel -- short-range accelerations by the tree walk.
+ *
+ * One warp walks the tree for 32 Hilbert-consecutive targets (the grouping
+ * idea of Sec. 2 and the 32-wide neighbour chunks of Sec. 2.1), keeping a
+ * per-target lane mask so that every target gets exactly its own opening
+ * decisions (the same as a per-particle walk).  OG_FP32_KAHAN: displacements
+ * are formed to FP64 accuracy from split-float positions and rounded to FP32,
+ * interactions run in FP32 on the special-function unit, per-target sums are
+ * Kahan-compensated; decisions that FP32 cannot settle are re-taken in FP64.
+ * OG_FP64: the same walk in double precision.
+ *
+ * r_s > 0 with rcut_factor * r_s < box / 2; theta >= 0
+ * acc          device out, float[n][3] (FP32_KAHAN) or double[n][3] (FP64),
+ *              original particle order
+ * n_interact   device out (optional, may be NULL): uint64 total number of
+ *              interactions (accepted nodes + particle pairs inside rcut)
+ * counts       device out (optional, may be NULL): int32[n] interactions per
+ *              particle, original order
+ * ws, ws_bytes device workspace of at least og_accel_ws_bytes(t, prec)
+ */
+og_status og_shortrange_accel(const og_tree* t, double r_s, double theta, og_precision prec, void* acc,
+                              uint64_t* n_interact, int32_t* counts, void* ws, size_t ws_bytes, og_stream stream);
+
+/*
+ * og_shortrange_adjoint -- dL/dx and dL/dm for L = sum_i w_i . a_i.
+ *
+ * The opening, cut and softening decisions of og_shortrange_accel are frozen
+ * (recomputed deterministically by the same walk).  With g(d) = -F(r) d and
+ * J = dg/dd = -F I - (F'/r) d d^T:
+ *   target side  dL/dx_i += sum_s M_s J(d_is) w_i
+ *   source side  for every term (i, s) and every particle k in s:
+ *                dL/dx_k -= m_k J(d_is) w_i,
+ *                dL/dm_k += w_i . g(d_is) - (J(d_is) w_i) . (x_k - X_s)
+ * (node centres of mass move with their members).  Source terms are summed
+ * per node in FP64 and pushed down the tree level by level.
+ *
+ * w            device, float[n][3] (original order)
+ * dpos         device out, double[n][3]; dmass device out, double[n]
+ * recompute_lists  must be 1 (interaction lists are recomputed; storing them
+ *              returns OG_ENOTIMPL)
+ * prec         OG_FP32_KAHAN (FP32 interactions; FP64 accumulators)
+ */
+og_status og_shortrange_adjoint(const og_tree* t, double r_s, double theta, og_precision prec, const float* w,
+                                double* dpos, double* dmass, int recompute_lists, void* ws, size_t ws_bytes,
+                                og_stream stream);
+
+/* Synchronise the stream and return the status recorded on the device in a
+ * workspace or tree buffer (any buffer sized by the helpers above). */
+og_status og_poll_status(const void* buf, og_stream stream);
+
+/* Synchronise and return the number of tree nodes (or -1 on error). */
+int64_t og_tree_node_count(const og_tree* t, og_stream stream);
+
+/* Copy node fields into caller device buffers (any may be NULL), nodes in
+ * the tree's internal order, first og_tree_node_count() entries valid:
+ * level, first (sorted particle index), count, parent (-1 for the root),
+ * mass (FP64), com (FP64 [.][3]), hmax (FP64), child_first, nchild. */
+og_status og_tree_copy_nodes(const og_tree* t, int32_t* level, int32_t* first, int32_t* count, int32_t* parent,
+                             double* mass, double* com, double* hmax, int32_t* child_first, int32_t* nchild,
+                             og_stream stream);
+
+const char* og_status_str(og_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OG_H */

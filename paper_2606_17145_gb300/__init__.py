@@ -1,0 +1,243 @@
+"""GB300-native short-range TreePM gravity: Python binding of libog.so.
+
+The functions mirror the C ABI in include/og.h (same names, same steps):
+
+    keys_sort(pos, box)                               -> keys, order
+    tree_build(keys, order, pos, mass, eps, box)      -> Tree
+    shortrange_accel(tree, r_s, theta, prec)          -> acc (+ interaction count)
+    shortrange_adjoint(tree, r_s, theta, w)           -> dpos, dmass
+    ShortRangeAccel.apply(pos, mass, eps, box, r_s, theta) (torch.autograd.Function)
+
+This layer only marshals arguments: every step runs in the CUDA kernels of
+libog.so.  PyTorch provides device memory and the current CUDA stream.
+Tensors must live on one CUDA device; positions/masses/softenings are float64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _native as N
+
+_lib = None
+
+
+def lib():
+    """The loaded libog.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        _lib = N.load()
+    return _lib
+
+
+class OGError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().og_status_str(code).decode() if code >= 0 else "unknown"
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+def _check(code: int, where: str):
+    if code != N.OG_OK:
+        raise OGError(code, where)
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _cuda(t: torch.Tensor, dtype, shape_tail=None, name="tensor"):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_tail is not None and tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"{name} must have shape [n, {', '.join(map(str, shape_tail))}]")
+    return t
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    ws = torch.empty(max(int(nbytes), 256) + 256, dtype=torch.uint8, device=device)
+    off = (-ws.data_ptr()) % 256
+    return ws[off:off + max(int(nbytes), 256)]
+
+
+def params(leaf_size: int = 8, rcut_factor: float = 4.5, node_capacity: int = 0,
+           max_walk_iters: int = 0) -> N.og_params:
+    p = N.og_params()
+    lib().og_params_default(C.byref(p))
+    p.leaf_size = leaf_size
+    p.rcut_factor = rcut_factor
+    p.node_capacity = node_capacity
+    p.max_walk_iters = max_walk_iters
+    return p
+
+
+def poll_status(buf: torch.Tensor, stream=None) -> int:
+    """Synchronise and return the device status of a workspace / tree buffer."""
+    return lib().og_poll_status(_ptr(buf), _stream(stream))
+
+
+def keys_sort(pos: torch.Tensor, box: float, stream=None, check: bool = True, ws: torch.Tensor | None = None):
+    """Hilbert keys (as non-negative int64; they are 63-bit) and order (int32)."""
+    _cuda(pos, torch.float64, (3,), "pos")
+    n = pos.shape[0]
+    L = lib()
+    need = L.og_keys_sort_ws_bytes(n)
+    if ws is None:
+        ws = _workspace(need, pos.device)
+    keys = torch.empty(n, dtype=torch.int64, device=pos.device)
+    order = torch.empty(n, dtype=torch.int32, device=pos.device)
+    _check(L.og_keys_sort(_ptr(pos), n, float(box), _ptr(keys), _ptr(order), _ptr(ws), ws.numel(),
+                          _stream(stream)), "og_keys_sort")
+    if check:
+        _check(poll_status(ws, stream), "og_keys_sort (device)")
+    return keys, order
+
+
+class Tree:
+    """A tree built by og_tree_build; owns its device buffer."""
+
+    def __init__(self, mem: torch.Tensor, header: N.og_tree, inputs):
+        self.mem = mem
+        self.header = header
+        self._inputs = inputs  # keep the input tensors alive while the tree is in use
+
+    @property
+    def n(self) -> int:
+        return int(self.header.n)
+
+    def node_count(self, stream=None) -> int:
+        return int(lib().og_tree_node_count(C.byref(self.header), _stream(stream)))
+
+    def nodes(self, stream=None) -> dict:
+        m = self.node_count(stream)
+        dev = self.mem.device
+        out = dict(level=torch.empty(m, dtype=torch.int32, device=dev),
+                   first=torch.empty(m, dtype=torch.int32, device=dev),
+                   count=torch.empty(m, dtype=torch.int32, device=dev),
+                   parent=torch.empty(m, dtype=torch.int32, device=dev),
+                   mass=torch.empty(m, dtype=torch.float64, device=dev),
+                   com=torch.empty((m, 3), dtype=torch.float64, device=dev),
+                   hmax=torch.empty(m, dtype=torch.float64, device=dev),
+                   child_first=torch.empty(m, dtype=torch.int32, device=dev),
+                   nchild=torch.empty(m, dtype=torch.int32, device=dev))
+        _check(lib().og_tree_copy_nodes(C.byref(self.header), *[_ptr(out[k]) for k in
+                                                                 ("level", "first", "count", "parent", "mass", "com",
+                                                                  "hmax", "child_first", "nchild")],
+                                        _stream(stream)), "og_tree_copy_nodes")
+        return out
+
+
+def tree_build(keys: torch.Tensor, order: torch.Tensor, pos: torch.Tensor, mass: torch.Tensor, eps, box: float,
+               p: N.og_params | None = None, stream=None, check: bool = True, mem: torch.Tensor | None = None) -> Tree:
+    """Octree over the sorted particles.  eps: float64 tensor [n] or a float."""
+    _cuda(pos, torch.float64, (3,), "pos")
+    _cuda(mass, torch.float64, None, "mass")
+    _cuda(keys, torch.int64, None, "keys")
+    _cuda(order, torch.int32, None, "order")
+    n = pos.shape[0]
+    L = lib()
+    p = p or params()
+    need = L.og_tree_bytes(n, C.byref(p))
+    if need == 0:
+        raise ValueError("invalid particle count or node capacity")
+    if mem is None:
+        mem = _workspace(need, pos.device)
+    if isinstance(eps, torch.Tensor):
+        _cuda(eps, torch.float64, None, "eps")
+        eps_t, eps_s = eps, 0.0
+    else:
+        eps_t, eps_s = None, float(eps)
+    hdr = N.og_tree()
+    _check(L.og_tree_build(_ptr(keys), _ptr(order), _ptr(pos), _ptr(mass), _ptr(eps_t), eps_s, n, float(box),
+                           C.byref(p), _ptr(mem), mem.numel(), C.byref(hdr), _stream(stream)), "og_tree_build")
+    if check:
+        _check(poll_status(mem, stream), "og_tree_build (device)")
+    return Tree(mem, hdr, (keys, order, pos, mass, eps_t))
+
+
+def shortrange_accel(tree: Tree, r_s: float, theta: float, prec: str = "fp32", counts: bool = False,
+                     stream=None, check: bool = True, ws: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                     total: torch.Tensor | None = None):
+    """Short-range accelerations (original order).  Returns (acc, total, counts)."""
+    L = lib()
+    code = N.OG_FP64 if prec == "fp64" else N.OG_FP32_KAHAN
+    dev = tree.mem.device
+    n = tree.n
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float64 if code == N.OG_FP64 else torch.float32, device=dev)
+    if total is None:
+        total = torch.zeros(1, dtype=torch.int64, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev) if counts else None
+    if ws is None:
+        ws = _workspace(L.og_accel_ws_bytes(C.byref(tree.header), code), dev)
+    _check(L.og_shortrange_accel(C.byref(tree.header), float(r_s), float(theta), code, _ptr(out), _ptr(total),
+                                 _ptr(cnt), _ptr(ws), ws.numel(), _stream(stream)), "og_shortrange_accel")
+    if check:
+        _check(poll_status(ws, stream), "og_shortrange_accel (device)")
+    return out, total, cnt
+
+
+def shortrange_adjoint(tree: Tree, r_s: float, theta: float, w: torch.Tensor, stream=None, check: bool = True,
+                       ws: torch.Tensor | None = None, dpos: torch.Tensor | None = None,
+                       dmass: torch.Tensor | None = None):
+    """dL/dx [n,3] and dL/dm [n] (float64, original order) for L = sum w . a."""
+    _cuda(w, torch.float32, (3,), "w")
+    L = lib()
+    dev = tree.mem.device
+    n = tree.n
+    if ws is None:
+        ws = _workspace(L.og_adjoint_ws_bytes(C.byref(tree.header), 1), dev)
+    if dpos is None:
+        dpos = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    if dmass is None:
+        dmass = torch.empty(n, dtype=torch.float64, device=dev)
+    _check(L.og_shortrange_adjoint(C.byref(tree.header), float(r_s), float(theta), N.OG_FP32_KAHAN, _ptr(w),
+                                   _ptr(dpos), _ptr(dmass), 1, _ptr(ws), ws.numel(), _stream(stream)),
+           "og_shortrange_adjoint")
+    if check:
+        _check(poll_status(ws, stream), "og_shortrange_adjoint (device)")
+    return dpos, dmass
+
+
+class ShortRangeAccel(torch.autograd.Function):
+    """acc = ShortRangeAccel.apply(pos, mass, eps, box, r_s, theta).
+
+    Forward: keys, sort, tree and the FP32-Kahan walk.  Backward: the adjoint
+    walk with the forward's opening / cut decisions frozen (recomputed on the
+    same tree), giving gradients for pos and mass.  eps may be a float or a
+    float64 tensor (it gets no gradient).
+    """
+
+    @staticmethod
+    def forward(ctx, pos, mass, eps, box, r_s, theta):
+        keys, order = keys_sort(pos, box, check=False)
+        tree = tree_build(keys, order, pos, mass, eps, box, check=False)
+        acc, total, _ = shortrange_accel(tree, r_s, theta, check=False)
+        _check(poll_status(tree.mem), "tree_build (device)")
+        ctx.tree = tree
+        ctx.r_s = r_s
+        ctx.theta = theta
+        ctx.total = total
+        return acc
+
+    @staticmethod
+    def backward(ctx, grad_acc):
+        w = grad_acc.contiguous().to(torch.float32)
+        dpos, dmass = shortrange_adjoint(ctx.tree, ctx.r_s, ctx.theta, w)
+        gm = dmass if ctx.needs_input_grad[1] else None
+        gp = dpos if ctx.needs_input_grad[0] else None
+        return gp, gm, None, None, None, None
+
+
+def shortrange_accel_autograd(pos, mass, eps, box, r_s, theta):
+    return ShortRangeAccel.apply(pos, mass, eps, box, r_s, theta)

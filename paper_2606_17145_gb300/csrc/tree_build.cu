@@ -1,0 +1,278 @@
+// tree_build.cu -- K3 permute, K4 level-by-level octree build, K5 walk groups.
+//
+// Nodes are stored level by level (level-major), so the children of a node are
+// a contiguous range of the next level.  A node is a maximal run of sorted
+// keys sharing the top 3*level bits; it is split (level < 21, more than
+// leaf_size members) into the runs of its 8 possible next digits.
+//
+// Top-down topology: one launch per level.  Eight lanes serve one parent; lane
+// d binary-searches the first key whose next digit is >= d inside the
+// parent's range, so the child runs come out without touching every key.
+// Child slots are taken per block with a single atomic on the level counter.
+//
+// Bottom-up moments: one launch per level, deepest first.  Eight lanes serve
+// one node; each lane reduces one child (or a strided share of a leaf's
+// particles) in FP64 and the eight partial sums are combined with shuffles in
+// a fixed order, so the result does not depend on scheduling.
+#include "og_internal.cuh"
+
+namespace og {
+
+
+__global__ void k_permute(BuildArgs A) {
+  const TreeDev& T = A.T;
+  const double L = A.L;
+  const double invL2 = 1.0 / (L * L);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < T.n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = A.order[k];
+    double w[3];
+    float hi[3], lo[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      w[c] = wrap_coord(A.pos[3 * (int64_t)i + c], L);
+      split_coord(w[c] / L, hi[c], lo[c]);
+      T.x64[3 * k + c] = w[c];
+    }
+    const double m = A.mass[i];
+    const double eps = A.eps ? A.eps[i] : A.eps_scalar;
+    if (!(isfinite(A.pos[3 * (int64_t)i]) && isfinite(A.pos[3 * (int64_t)i + 1]) &&
+          isfinite(A.pos[3 * (int64_t)i + 2]) && m > 0.0 && isfinite(m) && eps > 0.0 && isfinite(eps)))
+      set_status(T.sb, ST_BADINPUT);
+    const double h = 2.8 * eps;
+    const double hb = h / L;
+    T.m64[k] = m;
+    T.h64[k] = h;
+    T.order[k] = i;
+    T.pA[k] = make_float4(hi[0], hi[1], hi[2], (float)(m * invL2));
+    T.pB[k] = make_float4(lo[0], lo[1], lo[2], (float)(hb * hb));
+  }
+}
+
+__global__ void k_groups(TreeDev T, double L) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < T.ngroups; g += (int64_t)gridDim.x * blockDim.x) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    const int64_t a = g * kGroup, b = (T.n < a + kGroup ? T.n : a + kGroup);
+    for (int64_t k = a; k < b; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double x = T.x64[3 * k + c] / L;
+        lo[c] = fmin(lo[c], x);
+        hi[c] = fmax(hi[c], x);
+      }
+    T.gbox[2 * g] = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]), __double2float_rd(lo[2]), 0.f);
+    T.gbox[2 * g + 1] = make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]), __double2float_ru(hi[2]), 0.f);
+  }
+}
+
+__global__ void k_root(TreeDev T, int leaf_size) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    T.sb->magic = kMagicTree;
+    for (int l = 0; l < 24; ++l) T.sb->level_cnt[l] = 0;
+    T.sb->level_cnt[0] = 1;
+    const int leaf = (T.n <= leaf_size) ? 1 : 0;
+    T.nD[0] = make_int4(0, (int)T.n, -1, make_meta(0, 0, leaf));
+    T.nParent[0] = -1;
+  }
+}
+
+__device__ __forceinline__ int level_base(const StatusBlock* sb, int level) {
+  int b = 0;
+  for (int l = 0; l < level; ++l) b += sb->level_cnt[l];
+  return b;
+}
+
+// Expand level `lev` into level lev + 1.  256 threads = 32 parents per step.
+__global__ void __launch_bounds__(256) k_expand(TreeDev T, const uint64_t* __restrict__ keys, int lev, int leaf_size) {
+  __shared__ int s_cnt[32];
+  __shared__ int s_base;
+  const int base = level_base(T.sb, lev);
+  const int cnt = T.sb->level_cnt[lev];
+  const int next_base = base + cnt;
+  if (next_base > T.cap) return;  // capacity exceeded at an upper level (flagged there)
+  const int lane = threadIdx.x & 31;
+  const int sub = lane & 7;                      // digit handled by this lane
+  const int slot = threadIdx.x >> 3;             // parent slot in the block (0..31)
+  const int shift = 63 - 3 * (lev + 1);
+  for (int step = blockIdx.x * 32; step < cnt; step += gridDim.x * 32) {
+    const int p = base + step + slot;
+    const bool live = (step + slot) < cnt;
+    int4 D = make_int4(0, 0, -1, 0);
+    bool split = false;
+    if (live) {
+      D = T.nD[p];
+      split = !meta_leaf(D.w);
+    }
+    int start = 0, end = 0;
+    if (split) {
+      // first index in [f, f + c) whose digit at level lev+1 is >= sub
+      int lo = D.x, hi = D.x + D.y;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const uint32_t dg = (uint32_t)((keys[mid] >> shift) & 7u);
+        if (dg < (uint32_t)sub) lo = mid + 1; else hi = mid;
+      }
+      start = lo;
+    }
+    const int nxt = __shfl_down_sync(0xffffffffu, start, 1, 8);
+    end = (sub == 7) ? D.x + D.y : nxt;
+    const bool has = split && end > start;
+    const uint32_t seg = (__ballot_sync(0xffffffffu, has) >> (lane & 24)) & 0xffu;
+    const int nchild = __popc(seg);
+    const int rank = __popc(seg & ((1u << sub) - 1u));
+    // block-wide allocation of child slots
+    if (sub == 0) s_cnt[slot] = split ? nchild : 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int run = 0;
+      for (int s2 = 0; s2 < 32; ++s2) {
+        const int c = s_cnt[s2];
+        s_cnt[s2] = run;
+        run += c;
+      }
+      s_base = run ? atomicAdd(&T.sb->level_cnt[lev + 1], run) : 0;
+    }
+    __syncthreads();
+    const int child_first = next_base + s_base + s_cnt[slot];
+    if (split) {
+      const bool fits = child_first + nchild <= T.cap;
+      if (!fits) {
+        if (sub == 0) set_status(T.sb, ST_NOSPACE);
+      } else {
+        if (has) {
+          const int c = child_first + rank;
+          const int ccount = end - start;
+          const int leaf = (ccount <= leaf_size || lev + 1 >= kMaxLevel) ? 1 : 0;
+          T.nD[c] = make_int4(start, ccount, -1, make_meta(0, lev + 1, leaf));
+          T.nParent[c] = p;
+        }
+        if (sub == 0) {
+          D.z = child_first;
+          D.w = make_meta(nchild, lev, 0);
+          T.nD[p] = D;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Bottom-up moments for one level.  8 lanes per node.
+__global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, double L) {
+  const int base = level_base(T.sb, lev);
+  const int cnt = T.sb->level_cnt[lev];
+  if (base + cnt > T.cap) return;  // capacity already exceeded (flagged by k_expand)
+  const int sub = threadIdx.x & 7;
+  const double side = ldexp(L, -lev);
+  const float side_b = ldexpf(1.0f, -lev);
+  const double invL = 1.0 / L, invL2 = 1.0 / (L * L);
+  // warp-uniform loop bound: the 4 node groups of a warp stay together for the shuffles
+  const int stride = (gridDim.x * blockDim.x) >> 3;
+  for (int wstep = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3; wstep < cnt; wstep += stride) {
+    const int step = wstep + ((threadIdx.x & 31) >> 3);
+    const bool live = step < cnt;
+    const int p = base + step;
+    const int4 D = live ? T.nD[p] : make_int4(0, 0, -1, 0);
+    double M = 0.0, S0 = 0.0, S1 = 0.0, S2 = 0.0, H = 0.0;
+    if (!live) {
+    } else if (meta_leaf(D.w)) {
+      for (int j = D.x + sub; j < D.x + D.y; j += 8) {
+        const double m = T.m64[j];
+        M += m;
+        S0 += m * T.x64[3 * (int64_t)j];
+        S1 += m * T.x64[3 * (int64_t)j + 1];
+        S2 += m * T.x64[3 * (int64_t)j + 2];
+        H = fmax(H, T.h64[j]);
+        T.leaf_of[j] = p;
+      }
+    } else if (sub < meta_nchild(D.w)) {
+      const int c = D.z + sub;
+      M = T.mass64[c];
+      S0 = T.S64[3 * (int64_t)c];
+      S1 = T.S64[3 * (int64_t)c + 1];
+      S2 = T.S64[3 * (int64_t)c + 2];
+      H = T.hmax64[c];
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      M += __shfl_xor_sync(0xffffffffu, M, o, 8);
+      S0 += __shfl_xor_sync(0xffffffffu, S0, o, 8);
+      S1 += __shfl_xor_sync(0xffffffffu, S1, o, 8);
+      S2 += __shfl_xor_sync(0xffffffffu, S2, o, 8);
+      H = fmax(H, __shfl_xor_sync(0xffffffffu, H, o, 8));
+    }
+    if (live && sub == 0) {
+      const double com[3] = {S0 / M, S1 / M, S2 / M};
+      float hi[3], lo[3];
+      double cen[3];
+      float cenb[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        split_coord(com[c] * invL, hi[c], lo[c]);
+        const uint32_t q = quantise(T.x64[3 * (int64_t)D.x + c], L) >> (kMaxLevel - lev);
+        cen[c] = __dmul_rn((double)q + 0.5, side);
+        cenb[c] = ((float)q + 0.5f) * side_b;
+      }
+      const double hb = H * invL;
+      T.mass64[p] = M;
+      T.hmax64[p] = H;
+      T.S64[3 * (int64_t)p] = S0;
+      T.S64[3 * (int64_t)p + 1] = S1;
+      T.S64[3 * (int64_t)p + 2] = S2;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T.com64[3 * (int64_t)p + c] = com[c];
+        T.cen64[3 * (int64_t)p + c] = cen[c];
+      }
+      T.nA[p] = make_float4(hi[0], hi[1], hi[2], (float)(M * invL2));
+      T.nB[p] = make_float4(lo[0], lo[1], lo[2], (float)(hb * hb));
+      T.nC[p] = make_float4(cenb[0], cenb[1], cenb[2], side_b);
+    }
+  }
+}
+
+cudaError_t launch_tree_build(const BuildArgs& A, cudaStream_t s) {
+  const TreeDev& T = A.T;
+  int64_t grid = (T.n + 255) / 256;
+  if (grid > 152 * 32) grid = 152 * 32;
+  k_permute<<<(unsigned)grid, 256, 0, s>>>(A);
+  int64_t ggrid = (T.ngroups + 127) / 128;
+  if (ggrid > 152 * 16) ggrid = 152 * 16;
+  k_groups<<<(unsigned)ggrid, 128, 0, s>>>(T, A.L);
+  k_root<<<1, 32, 0, s>>>(T, A.leaf_size);
+  // Grids are fixed (the per-level node count lives on the device); blocks
+  // stride over the level.
+  const unsigned egrid = 152 * 8;
+  for (int lev = 0; lev < kMaxLevel; ++lev) k_expand<<<egrid, 256, 0, s>>>(T, A.keys, lev, A.leaf_size);
+  for (int lev = kMaxLevel; lev >= 0; --lev) k_moments<<<egrid, 256, 0, s>>>(T, lev, A.L);
+  return cudaGetLastError();
+}
+
+__global__ void k_copy_nodes(TreeDev T, int64_t m, int32_t* level, int32_t* first, int32_t* count, int32_t* parent,
+                             double* mass, double* com, double* hmax, int32_t* child_first, int32_t* nchild) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+    const int4 D = T.nD[p];
+    if (level) level[p] = meta_level(D.w);
+    if (first) first[p] = D.x;
+    if (count) count[p] = D.y;
+    if (parent) parent[p] = T.nParent[p];
+    if (mass) mass[p] = T.mass64[p];
+    if (com)
+      for (int c = 0; c < 3; ++c) com[3 * p + c] = T.com64[3 * p + c];
+    if (hmax) hmax[p] = T.hmax64[p];
+    if (child_first) child_first[p] = meta_leaf(D.w) ? -1 : D.z;
+    if (nchild) nchild[p] = meta_leaf(D.w) ? 0 : meta_nchild(D.w);
+  }
+}
+
+cudaError_t launch_copy_nodes(const TreeDev& T, int64_t m, int32_t* level, int32_t* first, int32_t* count,
+                              int32_t* parent, double* mass, double* com, double* hmax, int32_t* child_first,
+                              int32_t* nchild, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  int64_t grid = (m + 255) / 256;
+  if (grid > 152 * 16) grid = 152 * 16;
+  k_copy_nodes<<<(unsigned)grid, 256, 0, s>>>(T, m, level, first, count, parent, mass, com, hmax, child_first,
+                                              nchild);
+  return cudaGetLastError();
+}
+
+}  // namespace og
