@@ -1,0 +1,425 @@
+#!/usr/bin/env python3
+"""Benchmark of the short-range gravity hot path on one GB300 (or N replicas).
+
+One step = the whole path on one synthetic particle set with inputs resident
+in HBM: og_keys_sort -> og_tree_build -> og_shortrange_accel (FP32+Kahan) ->
+og_shortrange_adjoint (FP32, frozen decisions).  value = interactions per
+step / step time.  The all-FP64 walk (the comparison variant) is timed on
+the same tree in the same run and reported under "fp64".
+
+Default workload: 128^3 Zel'dovich-displaced lattice (P(k) ~ k^-2, rms
+displacement 0.5 cells), eps = 1/3840, r_s = 1.25/256, rcut = 4.5 r_s,
+theta = 0.5.  L2 is flushed (256 MiB write) between timed steps.
+
+--impl reference times the CPU oracle (single-threaded FP64) on a bounded
+sample of the same workload.  Under torchrun (N > 1) every rank runs an
+independent replica (no collective on the data path; "scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "short-range interactions/s and particles/s (fwd, fwd+adjoint) on 1 GB300, FP32 vs FP64"
+UNIT = "interactions/s"
+FWD_FLOPS = 51      # FP32 flops per forward interaction (FFMA = 2), counted from walk.cu
+ADJ_FLOPS = 75      # FP32 flops per adjoint interaction
+FWD_FP32_INSTR = 35  # FP32-pipe instructions per forward interaction (+2 MUFU)
+
+WORKLOADS = {
+    "zeldovich128": "128^3 Zel'dovich lattice, P(k)~k^-2, rms disp 0.5 cells, eps=1/3840, r_s=1.25/256, theta=0.5",
+    "nfw256": "256^3 clustered: 60% mass in 2000 NFW haloes, 40% uniform, eps=1/7680, r_s=1.25/512, theta=0.5",
+    "nfw128_adjoint": "128^3 clustered (NFW haloes + background), eps=1/3840, r_s=1.25/256, theta=0.5",
+    "zoom8m": "2^23 high-res NFW sphere + 2^21 low-res (64 m) background, eps 5e-5/2e-4, r_s=1.25/512, theta=0.5",
+    "uniform4096": "4096 uniform points, eps=1/480, r_s=1.25/16, theta=0.5",
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def walk_traffic(kernel_file="walk_fp32_zeldovich128.md"):
+    """DRAM bytes per launch of the forward walk from the committed ncu
+    summary, if it was taken on the current walk.cu (else None)."""
+    path = os.path.join(ROOT, "profiles", kernel_file)
+    src = os.path.join(ROOT, "paper_2606_17145_gb300", "csrc", "walk.cu")
+    try:
+        text = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m = re.search(r"walk\.cu sha256\[:16\]:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != digest:
+        return None
+    return float(t.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock / throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"og_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[2], parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["active_mask", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, _, flags in rows:
+            for nm, v in zip(names[1:], flags[1:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def oracle_throughput(w, theta, budget_s=12.0, min_targets=4096, seed=5):
+    """Single-threaded FP64 oracle forward walk on sampled targets (tree built
+    once, untimed).  Returns (interactions/s, particles/s, sample text)."""
+    import numpy as np
+    import oracle
+    t0 = time.time()
+    T = oracle.Tree(w.pos, w.mass, 2.8 * w.eps)
+    build_s = time.time() - t0
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(w.n)
+    done, inter, spent = 0, 0, 0.0
+    chunk = min_targets
+    while done < w.n and (spent < budget_s or done < min_targets):
+        tg = perm[done:done + chunk]
+        t1 = time.time()
+        _, cnt = T.walk(w.r_s, w.rcut, theta, tg)
+        spent += time.time() - t1
+        inter += int(cnt.sum())
+        done += len(tg)
+    T.close()
+    sample = (f"oracle tree walk (1 thread, FP64, -O2) of {done} random targets of the {w.n}-particle set "
+              f"(tree over all particles built once, {build_s:.1f} s, untimed); forward walk only")
+    return inter / spent, done / spent, sample, done, spent
+
+
+def run_reference(args, w, ws, rank):
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    oracle.build()
+    T = oracle.Tree(w.pos, w.mass, 2.8 * w.eps)
+    rng = np.random.default_rng(11)
+    per_step = args.ref_targets
+    times, inters = [], []
+    for it in range(args.warmup + args.steps):
+        tg = rng.choice(w.n, per_step, replace=False)
+        t0 = time.time()
+        _, cnt = T.walk(w.r_s, w.rcut, args.theta, tg)
+        dt = time.time() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            inters.append(int(cnt.sum()))
+    value = sum(inters) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": w.n, "theta": args.theta,
+                       "step": f"oracle forward walk of {per_step} random targets"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} random targets per step, tree over all {w.n} particles "
+                                       "built once (untimed); forward walk only"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="zeldovich128", choices=sorted(WORKLOADS))
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-targets", type=int, default=8192)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+
+    import numpy as np
+    import ics
+    w = ics.make(args.workload)
+
+    if args.impl == "reference":
+        return run_reference(args, w, ws, rank)
+
+    import torch
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.barrier()
+        __graft_entry__.build()
+    import paper_2606_17145_gb300 as og
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    L = og.lib()
+
+    # resident inputs, preallocated outputs and workspaces (no allocation in the timed region)
+    pos = torch.tensor(w.pos, dtype=torch.float64, device=dev)
+    mass = torch.tensor(w.mass, dtype=torch.float64, device=dev)
+    eps = torch.tensor(w.eps, dtype=torch.float64, device=dev)
+    wt = torch.tensor(ics.loss_weights(w.n, 2002), dtype=torch.float32, device=dev)
+    n = w.n
+    ws_keys = og._workspace(L.og_keys_sort_ws_bytes(n), dev)
+    keys = torch.empty(n, dtype=torch.int64, device=dev)
+    order = torch.empty(n, dtype=torch.int32, device=dev)
+    p = og.params()
+    import ctypes as C
+    tree_mem = og._workspace(L.og_tree_bytes(n, C.byref(p)), dev)
+    k0, o0 = og.keys_sort(pos, w.box, ws=ws_keys)
+    tree = og.tree_build(k0, o0, pos, mass, eps, w.box, p=p, mem=tree_mem)
+    ws_acc = og._workspace(L.og_accel_ws_bytes(C.byref(tree.header), 0), dev)
+    ws_adj = og._workspace(L.og_adjoint_ws_bytes(C.byref(tree.header), 1), dev)
+    acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    acc64 = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    total = torch.zeros(1, dtype=torch.int64, device=dev)
+    total64 = torch.zeros(1, dtype=torch.int64, device=dev)
+    dpos = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    dmass = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    state = {}
+
+    def step(ev=None):
+        k, o = og.keys_sort(pos, w.box, check=False, ws=ws_keys, keys=keys, order=order)
+        if ev: ev[1].record()
+        tr = og.tree_build(k, o, pos, mass, eps, w.box, p=p, check=False, mem=tree_mem)
+        if ev: ev[2].record()
+        og.shortrange_accel(tr, w.r_s, args.theta, check=False, ws=ws_acc, out=acc, total=total)
+        if ev: ev[3].record()
+        og.shortrange_adjoint(tr, w.r_s, args.theta, wt, check=False, ws=ws_adj, dpos=dpos, dmass=dmass)
+        state["tree"] = tr
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for buf, name in ((ws_keys, "keys_sort"), (tree_mem, "tree_build"), (ws_acc, "accel"), (ws_adj, "adjoint")):
+        code = og.poll_status(buf)
+        if code != 0:
+            raise SystemExit(f"{name} failed on the device: {L.og_status_str(code).decode()}")
+    interactions = int(total.item())
+
+    phases = ["keys_sort", "tree_build", "accel_fp32", "adjoint_fp32"]
+    per = {k: [] for k in phases}
+    step_ms = []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t_wall = time.time()
+        for _ in range(args.steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            ev[0].record()
+            step(ev)
+            ev[4].record()
+            torch.cuda.synchronize()
+            step_ms.append(ev[0].elapsed_time(ev[4]))
+            for i, k in enumerate(phases):
+                per[k].append(ev[i].elapsed_time(ev[i + 1]))
+        torch.cuda.synchronize()
+        wall = time.time() - t_wall
+    clocks = clk.summary()
+    ms = sum(step_ms) / len(step_ms)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * interactions / (ms * 1e-3)
+    pms = {k: sum(v) / len(v) for k, v in per.items()}
+
+    # FP64 walk on the same tree (comparison variant)
+    tr = state["tree"]
+    og.shortrange_accel(tr, w.r_s, args.theta, prec="fp64", check=False, ws=ws_acc, out=acc64, total=total64)
+    torch.cuda.synchronize()
+    f64 = []
+    for _ in range(args.fp64_steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        og.shortrange_accel(tr, w.r_s, args.theta, prec="fp64", check=False, ws=ws_acc, out=acc64, total=total64)
+        b.record()
+        torch.cuda.synchronize()
+        f64.append(a.elapsed_time(b))
+    f64_ms = sum(f64) / len(f64)
+    inter64 = int(total64.item())
+    code = og.poll_status(ws_acc)
+    if code != 0:
+        raise SystemExit(f"fp64 walk failed on the device: {L.og_status_str(code).decode()}")
+    rel = (acc.double() - acc64).norm(dim=1) / acc64.norm(dim=1).clamp_min(1e-300)
+    fp32_vs_fp64 = {"rms_rel": float(rel.pow(2).mean().sqrt()), "max_rel": float(rel.max())}
+
+    # end to end through the public API with host buffers
+    pos_h = pos.cpu().pin_memory()
+    mass_h = mass.cpu().pin_memory()
+    eps_h = eps.cpu().pin_memory()
+    wt_h = wt.cpu().pin_memory()
+    acc_h = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    dpos_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    dmass_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    h2d = pos_h.numel() * 8 + mass_h.numel() * 8 + eps_h.numel() * 8 + wt_h.numel() * 4
+    d2h = acc_h.numel() * 4 + dpos_h.numel() * 8 + dmass_h.numel() * 8
+
+    def e2e_step():
+        pos.copy_(pos_h, non_blocking=True)
+        mass.copy_(mass_h, non_blocking=True)
+        eps.copy_(eps_h, non_blocking=True)
+        wt.copy_(wt_h, non_blocking=True)
+        step()
+        acc_h.copy_(acc, non_blocking=True)
+        dpos_h.copy_(dpos, non_blocking=True)
+        dmass_h.copy_(dmass, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        e2e_step()
+        b.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+    if ws > 1:
+        t = torch.tensor([e2e_mean], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_mean = float(t.item())
+
+    # roofline of the dominant kernel (FP32 ALU bound; peak from unit counts and the max SM clock)
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FP32 FMA lanes x 2 x clock
+    walk = {"accel_fp32": (pms["accel_fp32"], FWD_FLOPS), "adjoint_fp32": (pms["adjoint_fp32"], ADJ_FLOPS)}
+    dom = max(walk, key=lambda k: walk[k][0])
+    dom_ms, dom_flops = walk[dom]
+    achieved = interactions * dom_flops / (dom_ms * 1e-3) / 1e12
+    traffic = walk_traffic() if dom == "accel_fp32" else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": traffic, "kernel": dom,
+                "flops_per_interaction": dom_flops,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz (max SM clock)"}
+
+    launches = og.LAUNCHES_PER_CALL
+    per_step_launches = (launches["keys_sort"] + launches["tree_build"] + launches["accel"] +
+                         launches["adjoint"])
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": n, "theta": args.theta,
+                   "step": "keys_sort + tree_build + accel_fp32 + adjoint_fp32 (inputs resident)",
+                   "l2": "flushed by a 256 MiB write between timed steps", "parallelism": f"replicas x{ws}"},
+        "clocks": clocks,
+        "e2e": {"value": ws * interactions / (e2e_mean * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
+        "gpu_launches": per_step_launches * args.steps,
+        "roofline": roofline,
+        "interactions_per_step": interactions,
+        "particles_per_s": ws * n / (ms * 1e-3),
+        "fwd_interactions_per_s": ws * interactions / (pms["accel_fp32"] * 1e-3),
+        "fwd_particles_per_s": ws * n / (pms["accel_fp32"] * 1e-3),
+        "breakdown_ms": pms,
+        "fp64": {"ms": f64_ms, "interactions_per_s": ws * inter64 / (f64_ms * 1e-3),
+                 "same_interactions": inter64 == interactions,
+                 "fp32_speedup": f64_ms / pms["accel_fp32"], "fp32_vs_fp64": fp32_vs_fp64},
+        "wall_s": wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, pps, sample, done, spent = oracle_throughput(w, args.theta)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                                "particles_per_s": pps}
+    if ws > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -22,6 +22,12 @@ from . import _native as N
 
 _lib = None
 
+# Kernels libog.so launches per call (fixed sequences, see csrc/): keys (1) +
+# 8 radix passes x (histogram, scan, scatter); permute + groups + root + 21
+# expand levels + 22 moment levels; one walk; adjoint walk + 22 push-down
+# levels + the particle gather.
+LAUNCHES_PER_CALL = {"keys_sort": 1 + 8 * 3, "tree_build": 3 + 21 + 22, "accel": 1, "adjoint": 1 + 22 + 1}
+
 
 def lib():
     """The loaded libog.so (raises if it has not been built)."""
@@ -86,7 +92,8 @@ def poll_status(buf: torch.Tensor, stream=None) -> int:
     return lib().og_poll_status(_ptr(buf), _stream(stream))
 
 
-def keys_sort(pos: torch.Tensor, box: float, stream=None, check: bool = True, ws: torch.Tensor | None = None):
+def keys_sort(pos: torch.Tensor, box: float, stream=None, check: bool = True, ws: torch.Tensor | None = None,
+              keys: torch.Tensor | None = None, order: torch.Tensor | None = None):
     """Hilbert keys (as non-negative int64; they are 63-bit) and order (int32)."""
     _cuda(pos, torch.float64, (3,), "pos")
     n = pos.shape[0]
@@ -94,8 +101,10 @@ def keys_sort(pos: torch.Tensor, box: float, stream=None, check: bool = True, ws
     need = L.og_keys_sort_ws_bytes(n)
     if ws is None:
         ws = _workspace(need, pos.device)
-    keys = torch.empty(n, dtype=torch.int64, device=pos.device)
-    order = torch.empty(n, dtype=torch.int32, device=pos.device)
+    if keys is None:
+        keys = torch.empty(n, dtype=torch.int64, device=pos.device)
+    if order is None:
+        order = torch.empty(n, dtype=torch.int32, device=pos.device)
     _check(L.og_keys_sort(_ptr(pos), n, float(box), _ptr(keys), _ptr(order), _ptr(ws), ws.numel(),
                           _stream(stream)), "og_keys_sort")
     if check:

@@ -246,7 +246,7 @@ struct WalkArgs {
   float uni_lim;               // bound for a warp-uniform periodic image
   float t_scale;               // t = r * t_scale - 1  (= u / 1.125 - 1)
   float ex2c;                  // exp(-u^2) = ex2(r2 * ex2c)
-  float fp_c;                  // f'(r)/r = fp_c * exp(-u^2)
+  float fp_c;                  // f'(r)/r = fp_c * r * exp(-u^2)
   // FP64, physical units (exact re-checks, FP64 walk)
   double rc2_64, th2_64, box, r_s64, inv2rs64, fp_c64;
   // outputs

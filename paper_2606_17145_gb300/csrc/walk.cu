@@ -132,7 +132,7 @@ __device__ __forceinline__ void force_f32(const WalkArgs& A, float r2, float h2,
   const float g = sr_poly(fmaf(r, A.t_scale, -1.0f));
   const float f = g * e;
   F = K * f;
-  if (DERIV) Fr = fmaf(Kp_r, f, K * (A.fp_c * e));
+  if (DERIV) Fr = fmaf(Kp_r, f, K * (A.fp_c * e * r));  // f'(r)/r = fp_c r exp(-u^2)
   else Fr = 0.0f;
 }
 
