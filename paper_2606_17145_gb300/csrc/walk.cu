@@ -24,7 +24,6 @@
 namespace og {
 
 constexpr int kWarpsPerBlock = 4;
-constexpr int kStack = 24;
 
 enum : int { DEC_DISCARD = 0, DEC_OPEN = 1, DEC_ACCEPT = 2, DEC_ACCEPT_OUT = 3, DEC_UNSURE = 4 };
 
@@ -151,8 +150,125 @@ __device__ __forceinline__ float warp_sum(float v, uint32_t m = 0xffffffffu) {
 
 struct GroupInfo {
   float cx, cy, cz;  // group box centre
-  float ex, ey, ez;  // group box half extents
+  float ex, ey, ez;  // group box half extents (padded outward)
 };
+
+// ------------------------------------------------------------------ per-warp shared buffers
+
+constexpr int kStack = 768;      // node entries (node, lane mask) per warp
+constexpr int kStackNeed = 256;  // a step pushes at most 32 nodes x 8 children
+constexpr int kQueue = 128;      // queued leaves / accepted nodes per warp
+constexpr int kQueueNeed = 64;   // a step queues at most 2 entries per node
+constexpr int kSlots = 32;       // sources staged per evaluation batch
+
+// Per-warp views of the block's shared arrays.  Queue entry: (first particle
+// or node, particle count or -1 for an accepted node, lane mask, image flags).
+// Image flags bit 0: one shift puts the whole entry at the minimum image of
+// every target of the group (bits 1-6: the shift per axis, 0 / +1 / -1).
+struct WarpBufs {
+  int2* stack;
+  int4* queue;
+  int* qoff;
+  double* slot;  // kSlots x 48 bytes: FP32 (float4 a, float4 b, int4 c) or FP64 (5 doubles + 2 ints)
+};
+
+enum : int { CL_NONE = -1, CL_DROP = 0, CL_OPEN = 1, CL_ACCEPT = 2, CL_MIXED = 3 };
+
+// Group-level classification of a node against the whole group box (box
+// units, FP32, conservative margins): DROP if the cube is beyond rcut of
+// every point of the box; OPEN if no point of the box can accept it; ACCEPT
+// if every point of the box accepts it (cube inside rcut, outside the 1.2x
+// cube, side < theta d); MIXED otherwise (exact per-lane decisions follow).
+__device__ __forceinline__ int classify(const WalkArgs& A, const GroupInfo& G, const float4& NC, const float4& NA,
+                                        const float4& NB) {
+  const float s = NC.w, hs = 0.5f * s;
+  const float tcx = fabsf(mi1(NC.x - G.cx)), tcy = fabsf(mi1(NC.y - G.cy)), tcz = fabsf(mi1(NC.z - G.cz));
+  const float gx = fmaxf(tcx - G.ex - hs, 0.f), gy = fmaxf(tcy - G.ey - hs, 0.f), gz = fmaxf(tcz - G.ez - hs, 0.f);
+  if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > A.grp_rc2) return CL_DROP;
+  if (s > 0.25f || G.ex > 0.125f || G.ey > 0.125f || G.ez > 0.125f) return CL_MIXED;
+  if (A.th2_hi == 0.0f) return CL_OPEN;  // theta = 0: nothing is ever accepted
+  const float txx = fabsf(mi1((NA.x - G.cx) + NB.x));
+  const float txy = fabsf(mi1((NA.y - G.cy) + NB.y));
+  const float txz = fabsf(mi1((NA.z - G.cz) + NB.z));
+  const float m_lo = 0.999f, m_hi = 1.001f;
+  const float ax = txx + G.ex, ay = txy + G.ey, az = txz + G.ez;
+  const float dmax2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
+  const float bx = fmaxf(txx - G.ex, 0.f), by = fmaxf(txy - G.ey, 0.f), bz = fmaxf(txz - G.ez, 0.f);
+  const float dmin2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+  const float fx0 = fmaxf(tcx - G.ex, 0.f) + hs, fy0 = fmaxf(tcy - G.ey, 0.f) + hs, fz0 = fmaxf(tcz - G.ez, 0.f) + hs;
+  const float minfar2 = fmaf(fx0, fx0, fmaf(fy0, fy0, fz0 * fz0));
+  const float fx1 = tcx + G.ex + hs, fy1 = tcy + G.ey + hs, fz1 = tcz + G.ez + hs;
+  const float maxfar2 = fmaf(fx1, fx1, fmaf(fy1, fy1, fz1 * fz1));
+  const float lim = 0.6f * s;
+  const bool all_inside = tcx + G.ex < lim * m_lo && tcy + G.ey < lim * m_lo && tcz + G.ez < lim * m_lo;
+  const bool all_outside = tcx - G.ex > lim * m_hi || tcy - G.ey > lim * m_hi || tcz - G.ez > lim * m_hi;
+  const float s2 = s * s;
+  if (s2 > A.th2_hi * dmax2 * m_hi || all_inside || minfar2 > A.rc2 * m_hi) return CL_OPEN;
+  if (s2 < A.th2_lo * dmin2 * m_lo && all_outside && maxfar2 < A.rc2 * m_lo) return CL_ACCEPT;
+  return CL_MIXED;
+}
+
+// Image shift that puts every (target, source) pair of an entry that can lie
+// inside rcut at its minimum image, if one exists for the whole cube.
+__device__ __forceinline__ int image_flags(const WalkArgs& A, const GroupInfo& G, const float4& NC) {
+  const float hs = 0.5f * NC.w;
+  const float dx = NC.x - G.cx, dy = NC.y - G.cy, dz = NC.z - G.cz;
+  const float nx = rintf(dx), ny = rintf(dy), nz = rintf(dz);
+  const bool uni = fabsf(dx - nx) + G.ex + hs < A.uni_lim && fabsf(dy - ny) + G.ey + hs < A.uni_lim &&
+                   fabsf(dz - nz) + G.ez + hs < A.uni_lim;
+  if (!uni) return 0;
+  const int cx = nx > 0.5f ? 1 : (nx < -0.5f ? 2 : 0);
+  const int cy = ny > 0.5f ? 1 : (ny < -0.5f ? 2 : 0);
+  const int cz = nz > 0.5f ? 1 : (nz < -0.5f ? 2 : 0);
+  return 1 | (cx << 1) | (cy << 3) | (cz << 5);
+}
+
+__device__ __forceinline__ float shift_of(int flags, int axis) {
+  const int c = (flags >> (1 + 2 * axis)) & 3;
+  return c == 1 ? 1.0f : (c == 2 ? -1.0f : 0.0f);
+}
+
+// Validates the queue and writes the slot offsets; returns the slot count or
+// -1 if an entry is malformed (then nothing may be evaluated).
+__device__ __forceinline__ int queue_offsets(const WalkArgs& A, const WarpBufs& W, int nq, int lane) {
+  int run = 0;
+  bool badq = false;
+  for (int b0 = 0; b0 < nq; b0 += 32) {
+    const int e = b0 + lane;
+    int c = 0;
+    if (e < nq) {
+      const int4 Q = W.queue[e];
+      if (Q.y == -1) {
+        c = 1;
+        badq = badq || Q.x < 0 || Q.x >= A.T.cap;
+      } else {
+        c = Q.y;
+        badq = badq || Q.y < 1 || Q.x < 0 || (int64_t)Q.x + Q.y > A.T.n;
+      }
+    }
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (e < nq) W.qoff[e] = run + incl - c;
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  __syncwarp();
+  if (__any_sync(0xffffffffu, badq)) return -1;
+  return run;
+}
+
+// Queue entry holding slot s (binary search over the slot offsets).
+__device__ __forceinline__ int entry_of(const WarpBufs& W, int nq, int s) {
+  int lo = 0, hi = nq - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (W.qoff[mid] <= s) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 // ------------------------------------------------------------------ lanes
 
@@ -160,24 +276,26 @@ struct GroupInfo {
 template <bool ADJ>
 struct LaneF32 {
   int64_t k;          // sorted index of this lane's target
+  bool valid;
   float xh[3], xl[3]; // split position
   float h2;           // own softening support squared (box units)
-  float d[3], d2;     // displacement to the last decided node's COM
   float P[3];         // partial sum since the last fold
   float S[3], C[3];   // Kahan total and compensation
   float w[3];         // adjoint weight
   int nint;
 
-  __device__ void init(const WalkArgs& A, int64_t kk, bool valid) {
+  __device__ void init(const WalkArgs& A, int64_t kk, bool v) {
     k = kk;
-    const float4 a = valid ? A.T.pA[kk] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 b = valid ? A.T.pB[kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+    valid = v;
+    const int64_t kc = v ? kk : 0;  // never form an out-of-range address
+    const float4 a = A.T.pA[kc];
+    const float4 b = A.T.pB[kc];
     xh[0] = a.x; xh[1] = a.y; xh[2] = a.z;
     xl[0] = b.x; xl[1] = b.y; xl[2] = b.z;
     h2 = b.w;
 #pragma unroll
     for (int c = 0; c < 3; ++c) { P[c] = 0.f; S[c] = 0.f; C[c] = 0.f; w[c] = 0.f; }
-    if (ADJ && valid) {
+    if (ADJ && v) {
       const int32_t i = A.T.order[kk];
 #pragma unroll
       for (int c = 0; c < 3; ++c) w[c] = A.w[3 * (int64_t)i + c];
@@ -185,10 +303,10 @@ struct LaneF32 {
     nint = 0;
   }
 
+  // Exact per-lane decision for a node (FP32 with an FP64 re-check in the band).
   __device__ int decide(const WalkArgs& A, int node, const int4& ND, const float4& NC) {
     const float s = NC.w, hs = 0.5f * s;
-    // the hi differences are exact, so the minimum image is applied before
-    // the lo parts are added (no loss of relative precision across the box edge)
+    // hi differences are exact: the minimum image is taken before the lo parts are added
     const float ax = fabsf(mi1(NC.x - xh[0]) - xl[0]);
     const float ay = fabsf(mi1(NC.y - xh[1]) - xl[1]);
     const float az = fabsf(mi1(NC.z - xh[2]) - xl[2]);
@@ -197,10 +315,10 @@ struct LaneF32 {
     if (e2 > A.rc2_hi) return DEC_DISCARD;
     const float4 NA = A.T.nA[node];
     const float4 NB = A.T.nB[node];
-    d[0] = mi1(xh[0] - NA.x) + (xl[0] - NB.x);
-    d[1] = mi1(xh[1] - NA.y) + (xl[1] - NB.y);
-    d[2] = mi1(xh[2] - NA.z) + (xl[2] - NB.z);
-    d2 = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+    const float d0 = mi1(xh[0] - NA.x) + (xl[0] - NB.x);
+    const float d1 = mi1(xh[1] - NA.y) + (xl[1] - NB.y);
+    const float dz = mi1(xh[2] - NA.z) + (xl[2] - NB.z);
+    const float d2 = fmaf(d0, d0, fmaf(d1, d1, dz * dz));
     int dec;
     if (e2 >= A.rc2_lo) {
       dec = DEC_UNSURE;
@@ -220,26 +338,37 @@ struct LaneF32 {
     return dec;
   }
 
-  // One interaction with source mass m (box units) at displacement dv.
-  __device__ __forceinline__ void term(const WalkArgs& A, const float* dv, float r2, float m, float hh2, float* jw,
-                                       float& wg) {
-    float F, Fr;
-    force_f32<ADJ>(A, r2, fmaxf(h2, hh2), F, Fr);
-    if (!ADJ) {
-      const float sc = -m * F;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) P[c] = fmaf(sc, dv[c], P[c]);
+  // Stage slot s of the queue into slot position `lane` of the batch buffer.
+  __device__ __forceinline__ void stage(const WalkArgs& A, const WarpBufs& W, int nq, int s, int lane) {
+    const int e = entry_of(W, nq, s);
+    const int4 Q = W.queue[e];
+    float4 a, b;
+    int id;
+    float lo, hi;
+    if (Q.y < 0) {
+      a = A.T.nA[Q.x];
+      b = A.T.nB[Q.x];
+      id = -2 - Q.x;
+      lo = hi = __int_as_float(0x7f800000);  // accepted node: inside the cut by decision
     } else {
-      const float dw = fmaf(dv[0], w[0], fmaf(dv[1], w[1], dv[2] * w[2]));
-      const float q = Fr * dw;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        jw[c] = -fmaf(F, w[c], q * dv[c]);
-        P[c] = fmaf(m, jw[c], P[c]);
-      }
-      wg = -F * dw;
+      const int j = Q.x + (s - W.qoff[e]);
+      a = A.T.pA[j];
+      b = A.T.pB[j];
+      id = j;
+      lo = A.pp_lo;
+      hi = A.pp_hi;
     }
-    ++nint;
+    if (Q.w & 1) {
+      a.x -= shift_of(Q.w, 0);
+      a.y -= shift_of(Q.w, 1);
+      a.z -= shift_of(Q.w, 2);
+    } else {
+      b.w = -b.w;  // negative h^2 marks "minimum image per pair"
+    }
+    float4* f = reinterpret_cast<float4*>(W.slot) + 3 * lane;
+    f[0] = a;
+    f[1] = b;
+    reinterpret_cast<int4*>(f)[2] = make_int4(id, Q.z, __float_as_int(lo), __float_as_int(hi));
   }
 
   __device__ __forceinline__ void fold() {
@@ -250,80 +379,76 @@ struct LaneF32 {
     }
   }
 
-  __device__ void node_term(const WalkArgs& A, int node, bool mine, uint32_t amask) {
-    float jw[3] = {0.f, 0.f, 0.f}, wg = 0.f;
-    if (mine) {
-      const float4 NA = A.T.nA[node];
-      const float4 NB = A.T.nB[node];
-      term(A, d, d2, NA.w, NB.w, jw, wg);
+  __device__ __forceinline__ void evaluate(const WalkArgs& A, const WarpBufs& W, int nq, int lane) {
+    const int total = queue_offsets(A, W, nq, lane);
+    if (total < 0) {
+      if (lane == 0) set_status(A.wsb, ST_TREELINK);
+      return;
     }
-    if (ADJ) {
-      const float g0 = warp_sum(jw[0]), g1 = warp_sum(jw[1]), g2 = warp_sum(jw[2]), sg = warp_sum(wg);
-      if ((threadIdx.x & 31) == (__ffs(amask) - 1)) {
-        atomicAdd(&A.Gn[3 * (int64_t)node], (double)g0);
-        atomicAdd(&A.Gn[3 * (int64_t)node + 1], (double)g1);
-        atomicAdd(&A.Gn[3 * (int64_t)node + 2], (double)g2);
-        atomicAdd(&A.Sn[node], (double)sg);
-      }
-    }
-    fold();
-  }
-
-  template <bool UNIFORM>
-  __device__ void leaf_loop(const WalkArgs& A, int j0, int jn, bool open, const float* sh) {
-    const float xs0 = xh[0] + sh[0], xs1 = xh[1] + sh[1], xs2 = xh[2] + sh[2];
-    for (int j = j0; j < j0 + jn; ++j) {
-      const float4 SA = A.T.pA[j];
-      const float4 SB = A.T.pB[j];
-      float jw[3] = {0.f, 0.f, 0.f}, wg = 0.f;
-      bool hit = false;
-      if (open && j != k) {
+    for (int base = 0; base < total; base += kSlots) {
+      const int cnt = min(kSlots, total - base);
+      if (lane < cnt) stage(A, W, nq, base + lane, lane);
+      __syncwarp();
+      const float4* f = reinterpret_cast<const float4*>(W.slot);
+      for (int t = 0; t < cnt; ++t) {
+        const float4 a = f[3 * t];
+        const float4 b = f[3 * t + 1];
+        const int4 c = reinterpret_cast<const int4*>(f)[3 * t + 2];
         float dv[3];
-        if (UNIFORM) {
-          dv[0] = (xs0 - SA.x) + (xl[0] - SB.x);
-          dv[1] = (xs1 - SA.y) + (xl[1] - SB.y);
-          dv[2] = (xs2 - SA.z) + (xl[2] - SB.z);
+        if (b.w >= 0.0f) {
+          dv[0] = (xh[0] - a.x) + (xl[0] - b.x);
+          dv[1] = (xh[1] - a.y) + (xl[1] - b.y);
+          dv[2] = (xh[2] - a.z) + (xl[2] - b.z);
         } else {
-          dv[0] = mi1(xh[0] - SA.x) + (xl[0] - SB.x);
-          dv[1] = mi1(xh[1] - SA.y) + (xl[1] - SB.y);
-          dv[2] = mi1(xh[2] - SA.z) + (xl[2] - SB.z);
+          dv[0] = mi1(xh[0] - a.x) + (xl[0] - b.x);
+          dv[1] = mi1(xh[1] - a.y) + (xl[1] - b.y);
+          dv[2] = mi1(xh[2] - a.z) + (xl[2] - b.z);
         }
         const float r2 = fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2]));
-        if (r2 < A.pp_lo) hit = true;
-        else if (r2 <= A.pp_hi) hit = pair_inside_exact(A, k, j);
-        if (hit) term(A, dv, r2, SA.w, SB.w, jw, wg);
-      }
-      if (ADJ) {
-        const uint32_t hm = __ballot_sync(0xffffffffu, hit);
-        if (hm) {
-          const float g0 = warp_sum(jw[0]), g1 = warp_sum(jw[1]), g2 = warp_sum(jw[2]), sg = warp_sum(wg);
-          if ((threadIdx.x & 31) == (__ffs(hm) - 1)) {
-            atomicAdd(&A.Gp[3 * (int64_t)j], (double)g0);
-            atomicAdd(&A.Gp[3 * (int64_t)j + 1], (double)g1);
-            atomicAdd(&A.Gp[3 * (int64_t)j + 2], (double)g2);
-            atomicAdd(&A.Sp[j], (double)sg);
+        bool hit = valid && ((c.y >> lane) & 1) && c.x != k;
+        if (hit && !(r2 < __int_as_float(c.z)))
+          hit = c.x >= 0 && r2 <= __int_as_float(c.w) && pair_inside_exact(A, k, c.x);
+        float jw[3] = {0.f, 0.f, 0.f}, wg = 0.f;
+        if (hit) {
+          float F, Fr;
+          force_f32<ADJ>(A, r2, fmaxf(h2, fabsf(b.w)), F, Fr);
+          if (!ADJ) {
+            const float sc = -a.w * F;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) P[q] = fmaf(sc, dv[q], P[q]);
+          } else {
+            const float dw = fmaf(dv[0], w[0], fmaf(dv[1], w[1], dv[2] * w[2]));
+            const float qq = Fr * dw;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              jw[q] = -fmaf(F, w[q], qq * dv[q]);
+              P[q] = fmaf(a.w, jw[q], P[q]);
+            }
+            wg = -F * dw;
+          }
+          ++nint;
+        }
+        if (ADJ) {
+          const uint32_t hm = __ballot_sync(0xffffffffu, hit);
+          if (hm) {
+            const float g0 = warp_sum(jw[0]), g1 = warp_sum(jw[1]), g2 = warp_sum(jw[2]), sg = warp_sum(wg);
+            if (lane == __ffs(hm) - 1) {
+              double* G = c.x >= 0 ? A.Gp + 3 * (int64_t)c.x : A.Gn + 3 * (int64_t)(-2 - c.x);
+              double* Sx = c.x >= 0 ? A.Sp + c.x : A.Sn + (-2 - c.x);
+              atomicAdd(G, (double)g0);
+              atomicAdd(G + 1, (double)g1);
+              atomicAdd(G + 2, (double)g2);
+              atomicAdd(Sx, (double)sg);
+            }
           }
         }
       }
+      fold();
+      __syncwarp();
     }
-    fold();
   }
 
-  __device__ void leaf(const WalkArgs& A, const int4& ND, const float4& NC, bool open, const GroupInfo& G) {
-    // A warp-uniform periodic image for the whole leaf exists when every
-    // (target, source) pair that can lie inside rcut is certainly put at its
-    // minimum image by one shift of the leaf.
-    const float hs = 0.5f * NC.w;
-    const float dx = NC.x - G.cx, dy = NC.y - G.cy, dz = NC.z - G.cz;
-    const float nx = rintf(dx), ny = rintf(dy), nz = rintf(dz);
-    const bool uni = fabsf(dx - nx) + G.ex + hs < A.uni_lim && fabsf(dy - ny) + G.ey + hs < A.uni_lim &&
-                     fabsf(dz - nz) + G.ez + hs < A.uni_lim;
-    const float sh[3] = {nx, ny, nz};
-    if (uni) leaf_loop<true>(A, ND.x, ND.y, open, sh);
-    else leaf_loop<false>(A, ND.x, ND.y, open, sh);
-  }
-
-  __device__ void finish(const WalkArgs& A, bool valid) {
+  __device__ void finish(const WalkArgs& A) {
     if (!valid) return;
     const int32_t i = A.T.order[k];
     if (!ADJ) {
@@ -337,22 +462,26 @@ struct LaneF32 {
   }
 };
 
-// FP64 lane (forward only): the same walk in double precision.
+// FP64 lane (forward only): the same traversal and decisions, double-precision
+// interactions with the library's erfc / exp, plain double sums.
 struct LaneF64 {
   int64_t k;
+  bool valid;
   double x[3];
   double h;
   double a[3];
   int nint;
 
-  __device__ void init(const WalkArgs& A, int64_t kk, bool valid) {
+  __device__ void init(const WalkArgs& A, int64_t kk, bool v) {
     k = kk;
+    valid = v;
+    const int64_t kc = v ? kk : 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      x[c] = valid ? A.T.x64[3 * kk + c] : 0.0;
+      x[c] = A.T.x64[3 * kc + c];
       a[c] = 0.0;
     }
-    h = valid ? A.T.h64[kk] : 0.0;
+    h = A.T.h64[kc];
     nint = 0;
   }
 
@@ -360,47 +489,77 @@ struct LaneF64 {
     return decide_exact(A, k, node, meta_level(ND.w));
   }
 
-  __device__ void term(const WalkArgs& A, const double* dv, double m, double hs) {
-    const double r2 = norm2_64(dv[0], dv[1], dv[2]);
-    const double r = sqrt(r2);
-    const double hh = fmax(h, hs);
-    double K;
-    if (r >= hh) {
-      K = 1.0 / (r * r * r);
+  // Slot layout (48 bytes): double x, y, z, m, h; int id, int mask.
+  __device__ __forceinline__ void stage(const WalkArgs& A, const WarpBufs& W, int nq, int s, int lane) {
+    const int e = entry_of(W, nq, s);
+    const int4 Q = W.queue[e];
+    double* d = W.slot + 6 * lane;
+    int* ii = reinterpret_cast<int*>(d + 5);
+    if (Q.y < 0) {
+      const int n = Q.x;
+      d[0] = A.T.com64[3 * (int64_t)n];
+      d[1] = A.T.com64[3 * (int64_t)n + 1];
+      d[2] = A.T.com64[3 * (int64_t)n + 2];
+      d[3] = A.T.mass64[n];
+      d[4] = A.T.hmax64[n];
+      ii[0] = -2 - n;
     } else {
-      const double v = r / hh;
-      const double h3 = 1.0 / (hh * hh * hh);
-      if (v < 0.5) K = h3 * (32.0 / 3.0 + v * v * (32.0 * v - 38.4));
-      else K = h3 * (64.0 / 3.0 - 48.0 * v + 38.4 * v * v - (32.0 / 3.0) * v * v * v - (1.0 / 15.0) / (v * v * v));
+      const int j = Q.x + (s - W.qoff[e]);
+      d[0] = A.T.x64[3 * (int64_t)j];
+      d[1] = A.T.x64[3 * (int64_t)j + 1];
+      d[2] = A.T.x64[3 * (int64_t)j + 2];
+      d[3] = A.T.m64[j];
+      d[4] = A.T.h64[j];
+      ii[0] = j;
     }
-    const double u = r * A.inv2rs64;
-    const double f = erfc(u) + 1.1283791670955126 * u * exp(-u * u);
-    const double sc = -m * K * f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) a[c] += sc * dv[c];
-    ++nint;
+    ii[1] = Q.z;
   }
 
-  __device__ void node_term(const WalkArgs& A, int node, bool mine, uint32_t) {
-    if (!mine) return;
-    double dv[3];
+  __device__ __forceinline__ void evaluate(const WalkArgs& A, const WarpBufs& W, int nq, int lane) {
+    const int total = queue_offsets(A, W, nq, lane);
+    if (total < 0) {
+      if (lane == 0) set_status(A.wsb, ST_TREELINK);
+      return;
+    }
+    const double L = A.box;
+    for (int base = 0; base < total; base += kSlots) {
+      const int cnt = min(kSlots, total - base);
+      if (lane < cnt) stage(A, W, nq, base + lane, lane);
+      __syncwarp();
+      for (int t = 0; t < cnt; ++t) {
+        const double* d = W.slot + 6 * t;
+        const int* ii = reinterpret_cast<const int*>(d + 5);
+        const int id = ii[0];
+        const bool mine = valid && ((ii[1] >> lane) & 1) && id != k;
+        double dv[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dv[c] = mi64(__dsub_rn(x[c], A.T.com64[3 * (int64_t)node + c]), A.box);
-    term(A, dv, A.T.mass64[node], A.T.hmax64[node]);
-  }
-
-  __device__ void leaf(const WalkArgs& A, const int4& ND, const float4&, bool open, const GroupInfo&) {
-    if (!open) return;
-    for (int j = ND.x; j < ND.x + ND.y; ++j) {
-      if (j == k) continue;
-      double dv[3];
+        for (int c = 0; c < 3; ++c) dv[c] = mi64(__dsub_rn(x[c], d[c]), L);
+        const double r2 = norm2_64(dv[0], dv[1], dv[2]);
+        if (mine && (id < 0 || r2 < A.rc2_64)) {
+          const double r = sqrt(r2);
+          const double hh = fmax(h, d[4]);
+          double K;
+          if (r >= hh) {
+            K = 1.0 / (r * r * r);
+          } else {
+            const double v = r / hh;
+            const double h3 = 1.0 / (hh * hh * hh);
+            if (v < 0.5) K = h3 * (32.0 / 3.0 + v * v * (32.0 * v - 38.4));
+            else K = h3 * (64.0 / 3.0 - 48.0 * v + 38.4 * v * v - (32.0 / 3.0) * v * v * v - (1.0 / 15.0) / (v * v * v));
+          }
+          const double u = r * A.inv2rs64;
+          const double f = erfc(u) + 1.1283791670955126 * u * exp(-u * u);
+          const double sc = -d[3] * K * f;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) dv[c] = mi64(__dsub_rn(x[c], A.T.x64[3 * (int64_t)j + c]), A.box);
-      if (norm2_64(dv[0], dv[1], dv[2]) < A.rc2_64) term(A, dv, A.T.m64[j], A.T.h64[j]);
+          for (int c = 0; c < 3; ++c) a[c] += sc * dv[c];
+          ++nint;
+        }
+      }
+      __syncwarp();
     }
   }
 
-  __device__ void finish(const WalkArgs& A, bool valid) {
+  __device__ void finish(const WalkArgs& A) {
     if (!valid) return;
     const int32_t i = A.T.order[k];
 #pragma unroll
@@ -413,9 +572,10 @@ struct LaneF64 {
 
 template <class Lane>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
-  __shared__ int s_first[kWarpsPerBlock][kStack];
-  __shared__ int s_cnt[kWarpsPerBlock][kStack];
-  __shared__ uint32_t s_mask[kWarpsPerBlock][kStack];
+  __shared__ int2 s_stack[kWarpsPerBlock][kStack];
+  __shared__ int4 s_queue[kWarpsPerBlock][kQueue];
+  __shared__ int s_qoff[kWarpsPerBlock][kQueue + 1];
+  __shared__ __align__(16) double s_slot[kWarpsPerBlock][kSlots * 6];
   const TreeDev& T = A.T;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t g = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
@@ -424,6 +584,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
     if (lane == 0) set_status(A.wsb, ST_NOTREE);
     return;
   }
+  WarpBufs W;
+  W.stack = s_stack[wib];
+  W.queue = s_queue[wib];
+  W.qoff = s_qoff[wib];
+  W.slot = s_slot[wib];
   int nodes_total = 0;
   for (int l = 0; l < kLevels; ++l) nodes_total += T.sb->level_cnt[l];
   if (nodes_total > T.cap) nodes_total = (int)T.cap;
@@ -431,6 +596,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   const int64_t k = g * kGroup + lane;
   const bool valid = k < T.n;
   const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+  const uint32_t lt = (1u << lane) - 1u;
 
   GroupInfo G;
   {
@@ -444,72 +610,117 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   Lane L;
   L.init(A, k, valid);
 
-  int* sf = s_first[wib];
-  int* sc = s_cnt[wib];
-  uint32_t* sm = s_mask[wib];
-  if (lane == 0) { sf[0] = 0; sc[0] = 1; sm[0] = vmask; }
-  int sp = 1;
-  long long iters = 0;
+  if (lane == 0) W.stack[0] = make_int2(0, (int)vmask);
+  int sp = 1, nq = 0;
+  long long visits = 0;
   __syncwarp();
-  while (sp > 0) {
-    if (++iters > A.max_iters) {
-      if (lane == 0) set_status(A.wsb, ST_WALKCAP);
-      break;
-    }
-    const int top = sp - 1;
-    const int node = sf[top];
-    const int cnt = sc[top];
-    const uint32_t mask = sm[top];
-    __syncwarp();
-    if (cnt > 1) {
-      if (lane == 0) { sf[top] = node + 1; sc[top] = cnt - 1; }
-    } else {
-      sp = top;
-    }
-    __syncwarp();
-    if (node < 0 || node >= nodes_total) {
-      if (lane == 0) set_status(A.wsb, ST_TREELINK);
-      break;
-    }
-    const float4 NC = T.nC[node];
-    {
-      // all lanes certainly discard: the node cube is beyond rcut of the group box
-      const float hs = 0.5f * NC.w;
-      const float gx = fmaxf(fabsf(mi1(NC.x - G.cx)) - hs - G.ex, 0.f);
-      const float gy = fmaxf(fabsf(mi1(NC.y - G.cy)) - hs - G.ey, 0.f);
-      const float gz = fmaxf(fabsf(mi1(NC.z - G.cz)) - hs - G.ez, 0.f);
-      if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > A.grp_rc2) continue;
-    }
-    const int4 ND = T.nD[node];
-    const bool active = (mask >> lane) & 1u;
-    const int dec = active ? L.decide(A, node, ND, NC) : DEC_DISCARD;
-    const uint32_t amask = __ballot_sync(0xffffffffu, dec == DEC_ACCEPT);
-    const uint32_t omask = __ballot_sync(0xffffffffu, dec == DEC_OPEN);
-    if (amask) L.node_term(A, node, dec == DEC_ACCEPT, amask);
-    if (omask) {
-      if (meta_leaf(ND.w)) {
-        if (ND.x < 0 || ND.y < 0 || (int64_t)ND.x + ND.y > T.n) {
-          if (lane == 0) set_status(A.wsb, ST_TREELINK);
-          break;
-        }
-        L.leaf(A, ND, NC, dec == DEC_OPEN, G);
-      } else {
-        const int nch = meta_nchild(ND.w);
-        if (nch <= 0 || ND.z <= node || ND.z + nch > nodes_total) {
-          if (lane == 0) set_status(A.wsb, ST_TREELINK);
-          break;
-        }
-        if (sp >= kStack) {
-          if (lane == 0) set_status(A.wsb, ST_STACK);
-          break;
-        }
-        if (lane == 0) { sf[sp] = ND.z; sc[sp] = nch; sm[sp] = omask; }
-        ++sp;
-        __syncwarp();
+  for (;;) {
+    if (sp > 0 && nq <= kQueue - kQueueNeed) {
+      if (sp > kStack - kStackNeed) {
+        if (lane == 0) set_status(A.wsb, ST_STACK);
+        break;
       }
+      // pop up to 32 nodes (the index is clamped so no lane forms an address
+      // outside the stack); every pop completes before any push
+      const int m = min(sp, 32);
+      const int2 E = W.stack[max(sp - 1 - lane, 0)];
+      __syncwarp();
+      const bool has = lane < m;
+      const int node = E.x;
+      const uint32_t mask = (uint32_t)E.y;
+      sp -= m;
+      visits += m;
+      if (visits > A.max_iters) {
+        if (lane == 0) set_status(A.wsb, ST_WALKCAP);
+        break;
+      }
+      if (__any_sync(0xffffffffu, has && (node < 0 || node >= nodes_total))) {
+        if (lane == 0) set_status(A.wsb, ST_TREELINK);
+        break;
+      }
+      const int nc = has ? node : 0;
+      const float4 NC = T.nC[nc];
+      const int4 ND = T.nD[nc];
+      const float4 NA = T.nA[nc];
+      const float4 NB = T.nB[nc];
+      const int cls = has ? classify(A, G, NC, NA, NB) : CL_NONE;
+      const bool leaf = meta_leaf(ND.w);
+      const int nch = meta_nchild(ND.w);
+      bool bad = false;
+      if (has && cls != CL_DROP) {
+        if (leaf) bad = ND.x < 0 || ND.y < 1 || (int64_t)ND.x + ND.y > T.n;
+        else bad = nch <= 0 || nch > 8 || ND.z <= node || ND.z + nch > nodes_total;
+      }
+      if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) set_status(A.wsb, ST_TREELINK);
+        break;
+      }
+      // OPEN internal nodes: push all children with the same lanes
+      const int npush = (cls == CL_OPEN && !leaf) ? nch : 0;
+      int incl = npush;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      for (int c = 0; c < npush; ++c) W.stack[sp + incl - npush + c] = make_int2(ND.z + c, (int)mask);
+      sp += __shfl_sync(0xffffffffu, incl, 31);
+      // OPEN leaves and ACCEPTed nodes: queue them for evaluation
+      const bool q = (cls == CL_OPEN && leaf) || cls == CL_ACCEPT;
+      const uint32_t qm = __ballot_sync(0xffffffffu, q);
+      if (q) {
+        const int fl = image_flags(A, G, NC);
+        W.queue[nq + __popc(qm & lt)] =
+            cls == CL_ACCEPT ? make_int4(node, -1, (int)mask, fl) : make_int4(ND.x, ND.y, (int)mask, fl);
+      }
+      nq += __popc(qm);
+      // MIXED nodes: exact per-lane decisions, one node at a time
+      uint32_t mm = __ballot_sync(0xffffffffu, cls == CL_MIXED);
+      while (mm) {
+        const int src = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const int mnode = __shfl_sync(0xffffffffu, node, src);
+        const uint32_t mmask = (uint32_t)__shfl_sync(0xffffffffu, (int)mask, src);
+        int4 MD;
+        MD.x = __shfl_sync(0xffffffffu, ND.x, src);
+        MD.y = __shfl_sync(0xffffffffu, ND.y, src);
+        MD.z = __shfl_sync(0xffffffffu, ND.z, src);
+        MD.w = __shfl_sync(0xffffffffu, ND.w, src);
+        float4 MC;
+        MC.x = __shfl_sync(0xffffffffu, NC.x, src);
+        MC.y = __shfl_sync(0xffffffffu, NC.y, src);
+        MC.z = __shfl_sync(0xffffffffu, NC.z, src);
+        MC.w = __shfl_sync(0xffffffffu, NC.w, src);
+        const bool act = valid && ((mmask >> lane) & 1u);
+        const int dec = act ? L.decide(A, mnode, MD, MC) : DEC_DISCARD;
+        const uint32_t am = __ballot_sync(0xffffffffu, dec == DEC_ACCEPT);
+        const uint32_t om = __ballot_sync(0xffffffffu, dec == DEC_OPEN);
+        const int fl = image_flags(A, G, MC);
+        if (am) {
+          if (lane == 0) W.queue[nq] = make_int4(mnode, -1, (int)am, fl);
+          ++nq;
+        }
+        if (om) {
+          if (meta_leaf(MD.w)) {
+            if (lane == 0) W.queue[nq] = make_int4(MD.x, MD.y, (int)om, fl);
+            ++nq;
+          } else {
+            const int mch = meta_nchild(MD.w);
+            if (lane < mch) W.stack[sp + lane] = make_int2(MD.z + lane, (int)om);
+            sp += mch;
+          }
+        }
+      }
+      __syncwarp();
+    } else if (nq > 0) {
+      L.evaluate(A, W, nq, lane);
+      nq = 0;
+      __syncwarp();
+    } else {
+      break;
     }
   }
-  L.finish(A, valid);
+  L.finish(A);
   if (A.total) {
     const unsigned cnt = __reduce_add_sync(0xffffffffu, (unsigned)(valid ? L.nint : 0));
     if (lane == 0 && cnt) atomicAdd(A.total, (unsigned long long)cnt);
