@@ -199,6 +199,33 @@ og_status og_shortrange_adjoint(const og_tree* t, double r_s, double theta, og_p
                                 double* dpos, double* dmass, int recompute_lists, void* ws, size_t ws_bytes,
                                 og_stream stream);
 
+/*
+ * og_keys_sort_noalloc -- og_keys_sort for callers that cannot allocate.
+ *
+ * The paper has no counterpart: this is a convenience of this library.  Some
+ * callers cannot call cudaMalloc, or are not allowed to: for example a host
+ * application that hands all GPU memory to its own pool and forbids libraries
+ * to allocate, or a loop that must not stall on an allocation.  This call
+ * computes exactly what og_keys_sort computes (same keys, same order) without
+ * a caller workspace: its scratch is a static device array of the library,
+ * sized for at most 2^20 particles (about 12.5 MiB), which every GPU that
+ * loads the library holds until the process exits.
+ *
+ * pos, n, box, keys_sorted, order, stream: as for og_keys_sort; n > 2^20
+ * returns OG_ENOSPACE (use og_keys_sort with a workspace for larger sets).
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (other streams
+ * or threads of the same process on the same device) race and must be
+ * ordered by the caller.  The array keeps the previous call's contents; the
+ * call clears what must start at zero.  There is no status word the caller
+ * can read: non-finite positions get key 0 (they sort first), so check
+ * positions beforehand if they may be non-finite.  Nothing is allocated or
+ * freed, and the stream is not synchronised.
+ */
+og_status og_keys_sort_noalloc(const double* pos, int64_t n, double box, uint64_t* keys_sorted, int32_t* order,
+                               og_stream stream);
+
 /* Synchronise the stream and return the status recorded on the device in a
  * workspace or tree buffer (any buffer sized by the helpers above). */
 og_status og_poll_status(const void* buf, og_stream stream);

@@ -259,3 +259,57 @@ cudaError_t launch_keys_sort(const double* pos, int64_t n, double L, uint64_t* k
 }
 
 }  // namespace og
+
+// ----------------------------------------------------------------------------
+// og_keys_sort_noalloc: the same keys and sort with the workspace in a static
+// device array instead of a caller buffer (declared in include/og.h).
+#include <cmath>
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 20;
+constexpr size_t noalloc_round(size_t x) { return (x + og::kAlign - 1) / og::kAlign * og::kAlign; }
+// Same carving as og::carve_sort: status block, alternate keys, alternate
+// indices, per-tile digit histograms, digit totals.
+constexpr size_t kNoAllocBytes =
+    noalloc_round(sizeof(og::StatusBlock)) + noalloc_round(sizeof(uint64_t) * kNoAllocMaxN) +
+    noalloc_round(sizeof(int32_t) * kNoAllocMaxN) +
+    noalloc_round(sizeof(uint32_t) * 256 * ((kNoAllocMaxN + og::kSortTile - 1) / og::kSortTile)) +
+    noalloc_round(sizeof(uint32_t) * 256);
+
+// Held by every GPU that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_sort_ws[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kNoAllocMaxDevices] = {};
+
+}  // namespace
+
+extern "C" og_status og_keys_sort_noalloc(const double* pos, int64_t n, double box, uint64_t* keys_sorted,
+                                          int32_t* order, og_stream stream) {
+  if (!pos || !keys_sorted || !order) return OG_EINVAL;
+  if (n < 1 || !std::isfinite(box) || !(box > 0.0)) return OG_EINVAL;
+  if (n > kNoAllocMaxN) return OG_ENOSPACE;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return OG_ECUDA;
+  void* base = nullptr;
+  {
+    // First call on this device: look up the device address of the static
+    // array (the host-side name is only a stand-in for it).
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_sort_ws) != cudaSuccess || !p) return OG_ECUDA;
+      g_noalloc_base[dev] = p;
+    }
+    base = g_noalloc_base[dev];
+  }
+  og::SortWs W;
+  if (og::carve_sort(base, n, &W) > kNoAllocBytes) return OG_ENOSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: the status block starts at zero
+  if (cudaMemsetAsync(W.sb, 0, sizeof(og::StatusBlock), s) != cudaSuccess) return OG_ECUDA;
+  return og::launch_keys_sort(pos, n, box, keys_sorted, order, W, s) == cudaSuccess ? OG_OK : OG_ECUDA;
+}
