@@ -197,7 +197,7 @@ def run_reference(args, w, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="zeldovich128", choices=sorted(WORKLOADS))
@@ -205,6 +205,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-targets", type=int, default=8192)
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-graph", action="store_true", help="launch every kernel instead of replaying a CUDA graph")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -271,6 +272,22 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # The library never allocates or synchronises inside a call and its grids
+    # are fixed (per-level sizes live on the device), so a whole step can be
+    # captured once and replayed as one CUDA graph.
+    graph = None
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+
+    def run_step(ev=None):
+        if graph is None or ev is not None:
+            step(ev)
+        else:
+            graph.replay()
     for buf, name in ((ws_keys, "keys_sort"), (tree_mem, "tree_build"), (ws_acc, "accel"), (ws_adj, "adjoint")):
         code = og.poll_status(buf)
         if code != 0:
@@ -287,16 +304,25 @@ def main():
         t_wall = time.time()
         for _ in range(args.steps):
             flush.zero_()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-            ev[0].record()
-            step(ev)
-            ev[4].record()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            run_step()
+            b.record()
             torch.cuda.synchronize()
-            step_ms.append(ev[0].elapsed_time(ev[4]))
-            for i, k in enumerate(phases):
-                per[k].append(ev[i].elapsed_time(ev[i + 1]))
+            step_ms.append(a.elapsed_time(b))
         torch.cuda.synchronize()
         wall = time.time() - t_wall
+    # per-phase breakdown (separately launched steps with events between phases)
+    for _ in range(min(args.steps, 10)):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record()
+        step(ev)
+        ev[4].record()
+        torch.cuda.synchronize()
+        for i, k in enumerate(phases):
+            per[k].append(ev[i].elapsed_time(ev[i + 1]))
     clocks = clk.summary()
     ms = sum(step_ms) / len(step_ms)
     if ws > 1:
@@ -344,7 +370,7 @@ def main():
         mass.copy_(mass_h, non_blocking=True)
         eps.copy_(eps_h, non_blocking=True)
         wt.copy_(wt_h, non_blocking=True)
-        step()
+        run_step()
         acc_h.copy_(acc, non_blocking=True)
         dpos_h.copy_(dpos, non_blocking=True)
         dmass_h.copy_(dmass, non_blocking=True)
@@ -392,7 +418,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": n, "theta": args.theta,
                    "step": "keys_sort + tree_build + accel_fp32 + adjoint_fp32 (inputs resident)",
-                   "l2": "flushed by a 256 MiB write between timed steps", "parallelism": f"replicas x{ws}"},
+                   "l2": "flushed by a 256 MiB write between timed steps", "parallelism": f"replicas x{ws}",
+                   "launch": "CUDA graph replay of the whole step" if graph is not None else "stream launches"},
         "clocks": clocks,
         "e2e": {"value": ws * interactions / (e2e_mean * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},

@@ -123,6 +123,7 @@ og_status og_tree_build(const uint64_t* keys_sorted, const int32_t* order, const
 
 static og_status walk_common(const og_tree* t, double r_s, double theta, WalkArgs& A) {
   if (!t || !t->built || !t->mem) return OG_ETREE;
+  if (t->node_capacity >= (int64_t(1) << 28)) return OG_EINVAL;  // the walk packs node indices in 28 bits
   if (!finite_pos(r_s) || !std::isfinite(theta) || theta < 0.0) return OG_EINVAL;
   const double L = t->box;
   const double rcut = t->rcut_factor * r_s;

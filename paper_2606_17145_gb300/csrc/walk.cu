@@ -2,12 +2,20 @@
 //
 // One warp walks the tree for one group of 32 Hilbert-consecutive targets
 // (lane = target).  The warp keeps a stack of (first node, node count, lane
-// mask) ranges in shared memory: a node is visited once per warp, every
-// active lane takes its own decision (discard / accept / open), and the
-// children of a node are pushed with the mask of the lanes that opened it.
-// Each target therefore receives exactly the terms of its own per-particle
-// walk (the rules are listed in og.h), while node data is read once per warp
-// and broadcast.
+// mask) ranges in shared memory and pops up to 32 nodes per step, one per
+// lane.  Each node is first classified against the bounding box of the whole
+// group (drop / open / accept / mixed); only mixed nodes take per-lane
+// decisions.  Opened internal nodes push their children as one range with the
+// mask of the lanes that opened them; opened leaves and accepted nodes are
+// queued.  Each target therefore receives exactly the terms of its own
+// per-particle walk (the rules are listed in og.h), while node data is read
+// once per warp.
+//
+// Evaluation.  Queued entries are expanded into source slots and staged in
+// shared memory 32 at a time.  The warp's lanes form four sub-groups of 8
+// consecutive targets; each sub-group evaluates only the staged sources whose
+// entry can reach its own (smaller) box, so distant halves of a group's
+// interaction list do not cost every lane.
 //
 // FP32 path.  Positions are split floats in box units (hi a multiple of 2^-23,
 // lo the rest), so hi_i - hi_j is exact and every displacement
@@ -17,7 +25,7 @@
 // reference, so decisions agree with an FP64 walk.  Interactions use the
 // special-function unit (rsqrt, ex2) and a polynomial for
 // erfcx(u) + 2u/sqrt(pi); per-target sums are Kahan-compensated after every
-// node visit.
+// batch of 32 staged sources.
 #include "og_internal.cuh"
 #include "short_range_poly.inc"
 
@@ -148,6 +156,19 @@ __device__ __forceinline__ float warp_sum(float v, uint32_t m = 0xffffffffu) {
   return v;
 }
 
+// Exact float -> double by bit manipulation on the integer pipe (the FP64
+// pipe is a small fraction of the FP32 rate on this GPU).  Subnormal inputs
+// flush to zero, like the FP32 arithmetic that produced them.
+__device__ __forceinline__ double f2d_exact(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const uint64_t exp = e == 0xffu ? 0x7ffull : (uint64_t)(e + (1023u - 127u));
+  const uint64_t man = (uint64_t)(u & 0x7fffffu) << 29;
+  const uint64_t bits = e == 0u ? sign : (sign | (exp << 52) | man);
+  return __longlong_as_double((long long)bits);
+}
+
 struct GroupInfo {
   float cx, cy, cz;  // group box centre
   float ex, ey, ez;  // group box half extents (padded outward)
@@ -155,12 +176,14 @@ struct GroupInfo {
 
 // ------------------------------------------------------------------ per-warp shared buffers
 
-constexpr int kStack = 768;      // node entries (node, lane mask) per warp
-constexpr int kStackNeed = 256;  // a step pushes at most 32 nodes x 8 children
+constexpr int kStack = 704;      // child-range entries per warp: >= 31 x 21 levels + one step
+constexpr int kStackNeed = 32;   // a step pushes at most one range per popped node
 constexpr int kQueue = 128;      // queued leaves / accepted nodes per warp
 constexpr int kQueueNeed = 64;   // a step queues at most 2 entries per node
 constexpr int kSlots = 32;       // sources staged per evaluation batch
 
+// Stack entry: (first node | node count << 28, lane mask); node indices stay
+// below 2^28 (checked on the host).
 // Per-warp views of the block's shared arrays.  Queue entry: (first particle
 // or node, particle count or -1 for an accepted node, lane mask, image flags).
 // Image flags bit 0: one shift puts the whole entry at the minimum image of
@@ -169,8 +192,16 @@ struct WarpBufs {
   int2* stack;
   int4* queue;
   int* qoff;
-  double* slot;  // kSlots x 48 bytes: FP32 (float4 a, float4 b, int4 c) or FP64 (5 doubles + 2 ints)
+  double* slot;          // kSlots x 48 bytes: FP32 (float4 a, float4 b, int4 c) or FP64 (5 doubles + 2 ints)
+  float4* sgbox;         // 4 sub-groups x (lo, hi) boxes of 8 consecutive targets
+  unsigned char* lists;  // 4 sub-groups x kSlots staged-slot indices
 };
+
+// Sub-groups: lanes 8g .. 8g+7 of a warp (8 Hilbert-consecutive targets).
+// A queued entry is evaluated only by the sub-groups whose targets can reach
+// it: its lane mask has bits in the sub-group and (for a leaf) its cube lies
+// within rcut of the sub-group's box.  Queue flags bits 8-11 hold that set.
+constexpr int kSub = 4;
 
 enum : int { CL_NONE = -1, CL_DROP = 0, CL_OPEN = 1, CL_ACCEPT = 2, CL_MIXED = 3 };
 
@@ -226,6 +257,26 @@ __device__ __forceinline__ int image_flags(const WalkArgs& A, const GroupInfo& G
 __device__ __forceinline__ float shift_of(int flags, int axis) {
   const int c = (flags >> (1 + 2 * axis)) & 3;
   return c == 1 ? 1.0f : (c == 2 ? -1.0f : 0.0f);
+}
+
+__device__ __forceinline__ int subgroup_bits(const WalkArgs& A, const WarpBufs& W, const float4& NC, uint32_t mask,
+                                             bool accepted) {
+  int bits = 0;
+#pragma unroll
+  for (int g = 0; g < kSub; ++g) {
+    if (((mask >> (8 * g)) & 0xffu) == 0u) continue;
+    if (accepted) {
+      bits |= 1 << g;
+      continue;
+    }
+    const float4 lo = W.sgbox[2 * g], hi = W.sgbox[2 * g + 1];
+    const float hs = 0.5f * NC.w;
+    const float gx = fmaxf(fabsf(mi1(NC.x - 0.5f * (lo.x + hi.x))) - 0.5f * (hi.x - lo.x) - hs, 0.f);
+    const float gy = fmaxf(fabsf(mi1(NC.y - 0.5f * (lo.y + hi.y))) - 0.5f * (hi.y - lo.y) - hs, 0.f);
+    const float gz = fmaxf(fabsf(mi1(NC.z - 0.5f * (lo.z + hi.z))) - 0.5f * (hi.z - lo.z) - hs, 0.f);
+    if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= A.grp_rc2) bits |= 1 << g;
+  }
+  return bits;
 }
 
 // Validates the queue and writes the slot offsets; returns the slot count or
@@ -338,8 +389,9 @@ struct LaneF32 {
     return dec;
   }
 
-  // Stage slot s of the queue into slot position `lane` of the batch buffer.
-  __device__ __forceinline__ void stage(const WalkArgs& A, const WarpBufs& W, int nq, int s, int lane) {
+  // Stage slot s of the queue into batch position `lane`; returns the
+  // sub-groups that evaluate it.
+  __device__ __forceinline__ int stage(const WalkArgs& A, const WarpBufs& W, int nq, int s, int lane) {
     const int e = entry_of(W, nq, s);
     const int4 Q = W.queue[e];
     float4 a, b;
@@ -369,6 +421,7 @@ struct LaneF32 {
     f[0] = a;
     f[1] = b;
     reinterpret_cast<int4*>(f)[2] = make_int4(id, Q.z, __float_as_int(lo), __float_as_int(hi));
+    return (Q.w >> 8) & 0xf;
   }
 
   __device__ __forceinline__ void fold() {
@@ -379,72 +432,69 @@ struct LaneF32 {
     }
   }
 
-  __device__ __forceinline__ void evaluate(const WalkArgs& A, const WarpBufs& W, int nq, int lane) {
-    const int total = queue_offsets(A, W, nq, lane);
-    if (total < 0) {
-      if (lane == 0) set_status(A.wsb, ST_TREELINK);
-      return;
+  // One (target, staged source) pair; `has` is false for idle lanes.  In the
+  // adjoint the source-side terms are summed over the lanes of the sub-group
+  // (all of which hold the same slot) and added once.
+  __device__ __forceinline__ void pair(const WalkArgs& A, const WarpBufs& W, int t, bool has, int lane) {
+    const float4* f = reinterpret_cast<const float4*>(W.slot);
+    const float4 a = f[3 * t];
+    const float4 b = f[3 * t + 1];
+    const int4 c = reinterpret_cast<const int4*>(f)[3 * t + 2];
+    float dh0 = xh[0] - a.x, dh1 = xh[1] - a.y, dh2 = xh[2] - a.z;
+    if (b.w < 0.0f) {
+      dh0 = mi1(dh0);
+      dh1 = mi1(dh1);
+      dh2 = mi1(dh2);
     }
-    for (int base = 0; base < total; base += kSlots) {
-      const int cnt = min(kSlots, total - base);
-      if (lane < cnt) stage(A, W, nq, base + lane, lane);
-      __syncwarp();
-      const float4* f = reinterpret_cast<const float4*>(W.slot);
-      for (int t = 0; t < cnt; ++t) {
-        const float4 a = f[3 * t];
-        const float4 b = f[3 * t + 1];
-        const int4 c = reinterpret_cast<const int4*>(f)[3 * t + 2];
-        float dv[3];
-        if (b.w >= 0.0f) {
-          dv[0] = (xh[0] - a.x) + (xl[0] - b.x);
-          dv[1] = (xh[1] - a.y) + (xl[1] - b.y);
-          dv[2] = (xh[2] - a.z) + (xl[2] - b.z);
-        } else {
-          dv[0] = mi1(xh[0] - a.x) + (xl[0] - b.x);
-          dv[1] = mi1(xh[1] - a.y) + (xl[1] - b.y);
-          dv[2] = mi1(xh[2] - a.z) + (xl[2] - b.z);
-        }
-        const float r2 = fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2]));
-        bool hit = valid && ((c.y >> lane) & 1) && c.x != k;
-        if (hit && !(r2 < __int_as_float(c.z)))
-          hit = c.x >= 0 && r2 <= __int_as_float(c.w) && pair_inside_exact(A, k, c.x);
-        float jw[3] = {0.f, 0.f, 0.f}, wg = 0.f;
-        if (hit) {
-          float F, Fr;
-          force_f32<ADJ>(A, r2, fmaxf(h2, fabsf(b.w)), F, Fr);
-          if (!ADJ) {
-            const float sc = -a.w * F;
+    float dv[3];
+    dv[0] = dh0 + (xl[0] - b.x);
+    dv[1] = dh1 + (xl[1] - b.y);
+    dv[2] = dh2 + (xl[2] - b.z);
+    const float r2 = fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2]));
+    bool hit = has && valid && ((c.y >> lane) & 1) && c.x != k;
+    if (hit && !(r2 < __int_as_float(c.z)))
+      hit = c.x >= 0 && r2 <= __int_as_float(c.w) && pair_inside_exact(A, k, c.x);
+    float jw[3] = {0.f, 0.f, 0.f}, wg = 0.f;
+    if (hit) {
+      float F, Fr;
+      force_f32<ADJ>(A, r2, fmaxf(h2, fabsf(b.w)), F, Fr);
+      if (!ADJ) {
+        const float sc = -a.w * F;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) P[q] = fmaf(sc, dv[q], P[q]);
-          } else {
-            const float dw = fmaf(dv[0], w[0], fmaf(dv[1], w[1], dv[2] * w[2]));
-            const float qq = Fr * dw;
+        for (int q = 0; q < 3; ++q) P[q] = fmaf(sc, dv[q], P[q]);
+      } else {
+        const float dw = fmaf(dv[0], w[0], fmaf(dv[1], w[1], dv[2] * w[2]));
+        const float qq = Fr * dw;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              jw[q] = -fmaf(F, w[q], qq * dv[q]);
-              P[q] = fmaf(a.w, jw[q], P[q]);
-            }
-            wg = -F * dw;
-          }
-          ++nint;
+        for (int q = 0; q < 3; ++q) {
+          jw[q] = -fmaf(F, w[q], qq * dv[q]);
+          P[q] = fmaf(a.w, jw[q], P[q]);
         }
-        if (ADJ) {
-          const uint32_t hm = __ballot_sync(0xffffffffu, hit);
-          if (hm) {
-            const float g0 = warp_sum(jw[0]), g1 = warp_sum(jw[1]), g2 = warp_sum(jw[2]), sg = warp_sum(wg);
-            if (lane == __ffs(hm) - 1) {
-              double* G = c.x >= 0 ? A.Gp + 3 * (int64_t)c.x : A.Gn + 3 * (int64_t)(-2 - c.x);
-              double* Sx = c.x >= 0 ? A.Sp + c.x : A.Sn + (-2 - c.x);
-              atomicAdd(G, (double)g0);
-              atomicAdd(G + 1, (double)g1);
-              atomicAdd(G + 2, (double)g2);
-              atomicAdd(Sx, (double)sg);
-            }
-          }
+        wg = -F * dw;
+      }
+      ++nint;
+    }
+    if (ADJ) {
+      const uint32_t hm = __ballot_sync(0xffffffffu, hit);
+      if (hm) {
+        float g0 = jw[0], g1 = jw[1], g2 = jw[2], sg = wg;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+          g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+          g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+          sg += __shfl_xor_sync(0xffffffffu, sg, o);
+        }
+        const uint32_t seg = (hm >> (lane & 24)) & 0xffu;
+        if (seg && (lane & 7) == __ffs(seg) - 1) {
+          double* G = c.x >= 0 ? A.Gp + 3 * (int64_t)c.x : A.Gn + 3 * (int64_t)(-2 - c.x);
+          double* Sx = c.x >= 0 ? A.Sp + c.x : A.Sn + (-2 - c.x);
+          atomicAdd(G, f2d_exact(g0));
+          atomicAdd(G + 1, f2d_exact(g1));
+          atomicAdd(G + 2, f2d_exact(g2));
+          atomicAdd(Sx, f2d_exact(sg));
         }
       }
-      fold();
-      __syncwarp();
     }
   }
 
@@ -490,7 +540,7 @@ struct LaneF64 {
   }
 
   // Slot layout (48 bytes): double x, y, z, m, h; int id, int mask.
-  __device__ __forceinline__ void stage(const WalkArgs& A, const WarpBufs& W, int nq, int s, int lane) {
+  __device__ __forceinline__ int stage(const WalkArgs& A, const WarpBufs& W, int nq, int s, int lane) {
     const int e = entry_of(W, nq, s);
     const int4 Q = W.queue[e];
     double* d = W.slot + 6 * lane;
@@ -513,50 +563,39 @@ struct LaneF64 {
       ii[0] = j;
     }
     ii[1] = Q.z;
+    return (Q.w >> 8) & 0xf;
   }
 
-  __device__ __forceinline__ void evaluate(const WalkArgs& A, const WarpBufs& W, int nq, int lane) {
-    const int total = queue_offsets(A, W, nq, lane);
-    if (total < 0) {
-      if (lane == 0) set_status(A.wsb, ST_TREELINK);
-      return;
-    }
-    const double L = A.box;
-    for (int base = 0; base < total; base += kSlots) {
-      const int cnt = min(kSlots, total - base);
-      if (lane < cnt) stage(A, W, nq, base + lane, lane);
-      __syncwarp();
-      for (int t = 0; t < cnt; ++t) {
-        const double* d = W.slot + 6 * t;
-        const int* ii = reinterpret_cast<const int*>(d + 5);
-        const int id = ii[0];
-        const bool mine = valid && ((ii[1] >> lane) & 1) && id != k;
-        double dv[3];
+  __device__ __forceinline__ void fold() {}
+
+  __device__ __forceinline__ void pair(const WalkArgs& A, const WarpBufs& W, int t, bool has, int lane) {
+    const double* d = W.slot + 6 * t;
+    const int* ii = reinterpret_cast<const int*>(d + 5);
+    const int id = ii[0];
+    const bool mine = has && valid && ((ii[1] >> lane) & 1) && id != k;
+    if (!mine) return;
+    double dv[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dv[c] = mi64(__dsub_rn(x[c], d[c]), L);
-        const double r2 = norm2_64(dv[0], dv[1], dv[2]);
-        if (mine && (id < 0 || r2 < A.rc2_64)) {
-          const double r = sqrt(r2);
-          const double hh = fmax(h, d[4]);
-          double K;
-          if (r >= hh) {
-            K = 1.0 / (r * r * r);
-          } else {
-            const double v = r / hh;
-            const double h3 = 1.0 / (hh * hh * hh);
-            if (v < 0.5) K = h3 * (32.0 / 3.0 + v * v * (32.0 * v - 38.4));
-            else K = h3 * (64.0 / 3.0 - 48.0 * v + 38.4 * v * v - (32.0 / 3.0) * v * v * v - (1.0 / 15.0) / (v * v * v));
-          }
-          const double u = r * A.inv2rs64;
-          const double f = erfc(u) + 1.1283791670955126 * u * exp(-u * u);
-          const double sc = -d[3] * K * f;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) a[c] += sc * dv[c];
-          ++nint;
-        }
-      }
-      __syncwarp();
+    for (int c = 0; c < 3; ++c) dv[c] = mi64(__dsub_rn(x[c], d[c]), A.box);
+    const double r2 = norm2_64(dv[0], dv[1], dv[2]);
+    if (id >= 0 && !(r2 < A.rc2_64)) return;
+    const double r = sqrt(r2);
+    const double hh = fmax(h, d[4]);
+    double K;
+    if (r >= hh) {
+      K = 1.0 / (r * r * r);
+    } else {
+      const double v = r / hh;
+      const double h3 = 1.0 / (hh * hh * hh);
+      if (v < 0.5) K = h3 * (32.0 / 3.0 + v * v * (32.0 * v - 38.4));
+      else K = h3 * (64.0 / 3.0 - 48.0 * v + 38.4 * v * v - (32.0 / 3.0) * v * v * v - (1.0 / 15.0) / (v * v * v));
     }
+    const double u = r * A.inv2rs64;
+    const double f = erfc(u) + 1.1283791670955126 * u * exp(-u * u);
+    const double sc = -d[3] * K * f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[c] += sc * dv[c];
+    ++nint;
   }
 
   __device__ void finish(const WalkArgs& A) {
@@ -568,6 +607,44 @@ struct LaneF64 {
   }
 };
 
+// ------------------------------------------------------------------ evaluation
+
+// Evaluate the queued entries: stage 32 sources at a time; each sub-group
+// walks the list of staged sources that can reach it.
+template <class Lane>
+__device__ __forceinline__ void evaluate_queue(const WalkArgs& A, const WarpBufs& W, int nq, int lane, Lane& L) {
+  const int total = queue_offsets(A, W, nq, lane);
+  if (total < 0) {
+    if (lane == 0) set_status(A.wsb, ST_TREELINK);
+    return;
+  }
+  const int sg = lane >> 3;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (int base = 0; base < total; base += kSlots) {
+    const int cnt = min(kSlots, total - base);
+    int bits = 0;
+    if (lane < cnt) bits = L.stage(A, W, nq, base + lane, lane);
+    int my_n = 0, iters = 0;
+#pragma unroll
+    for (int g = 0; g < kSub; ++g) {
+      const bool in = ((bits >> g) & 1) != 0;
+      const uint32_t m = __ballot_sync(0xffffffffu, in);
+      if (in) W.lists[g * kSlots + __popc(m & lt)] = (unsigned char)lane;
+      const int ng = __popc(m);
+      if (g == sg) my_n = ng;
+      iters = max(iters, ng);
+    }
+    __syncwarp();
+    for (int t = 0; t < iters; ++t) {
+      const bool has = t < my_n;
+      const int slot = has ? (int)W.lists[sg * kSlots + t] : 0;
+      L.pair(A, W, slot, has, lane);
+    }
+    L.fold();
+    __syncwarp();
+  }
+}
+
 // ------------------------------------------------------------------ traversal
 
 template <class Lane>
@@ -576,6 +653,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   __shared__ int4 s_queue[kWarpsPerBlock][kQueue];
   __shared__ int s_qoff[kWarpsPerBlock][kQueue + 1];
   __shared__ __align__(16) double s_slot[kWarpsPerBlock][kSlots * 6];
+  __shared__ float4 s_sgbox[kWarpsPerBlock][2 * kSub];
+  __shared__ unsigned char s_lists[kWarpsPerBlock][kSub * kSlots];
   const TreeDev& T = A.T;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t g = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
@@ -589,6 +668,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   W.queue = s_queue[wib];
   W.qoff = s_qoff[wib];
   W.slot = s_slot[wib];
+  W.sgbox = s_sgbox[wib];
+  W.lists = s_lists[wib];
   int nodes_total = 0;
   for (int l = 0; l < kLevels; ++l) nodes_total += T.sb->level_cnt[l];
   if (nodes_total > T.cap) nodes_total = (int)T.cap;
@@ -610,7 +691,30 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   Lane L;
   L.init(A, k, valid);
 
-  if (lane == 0) W.stack[0] = make_int2(0, (int)vmask);
+  {
+    // bounding box of each sub-group of 8 targets (box units, padded outward)
+    const float4 pa = T.pA[valid ? k : 0], pb = T.pB[valid ? k : 0];
+    float lo[3] = {pa.x + pb.x, pa.y + pb.y, pa.z + pb.z};
+    float hi[3] = {lo[0], lo[1], lo[2]};
+    if (!valid) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { lo[c] = 1e30f; hi[c] = -1e30f; }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+        hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+      }
+    if ((lane & 7) == 0) {
+      const float pad = 2e-7f;
+      W.sgbox[2 * (lane >> 3)] = make_float4(lo[0] - pad, lo[1] - pad, lo[2] - pad, 0.f);
+      W.sgbox[2 * (lane >> 3) + 1] = make_float4(hi[0] + pad, hi[1] + pad, hi[2] + pad, 0.f);
+    }
+  }
+
+  if (lane == 0) W.stack[0] = make_int2((int)(1u << 28), (int)vmask);  // the root: node 0, one node
   int sp = 1, nq = 0;
   long long visits = 0;
   __syncwarp();
@@ -620,20 +724,49 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
         if (lane == 0) set_status(A.wsb, ST_STACK);
         break;
       }
-      // pop up to 32 nodes (the index is clamped so no lane forms an address
-      // outside the stack); every pop completes before any push
+      // Pop whole child ranges from the top until up to 32 nodes are gathered.
+      // The index is clamped so no lane forms an address outside the stack,
+      // and every pop completes before any push.
       const int m = min(sp, 32);
       const int2 E = W.stack[max(sp - 1 - lane, 0)];
       __syncwarp();
-      const bool has = lane < m;
-      const int node = E.x;
-      const uint32_t mask = (uint32_t)E.y;
-      sp -= m;
-      visits += m;
+      const uint32_t ex = (uint32_t)E.x;
+      const int rcnt = lane < m ? (int)(ex >> 28) : 0;
+      const int rfirst_l = (int)(ex & 0x0fffffffu);
+      if (__any_sync(0xffffffffu, lane < m && (rcnt < 1 || rcnt > 8))) {
+        if (lane == 0) set_status(A.wsb, ST_TREELINK);
+        break;
+      }
+      int incl = rcnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int take = __popc(__ballot_sync(0xffffffffu, lane < m && incl <= 32));  // >= 4 ranges or all
+      const int total = __shfl_sync(0xffffffffu, incl, take - 1);
+      sp -= take;
+      visits += total;
       if (visits > A.max_iters) {
         if (lane == 0) set_status(A.wsb, ST_WALKCAP);
         break;
       }
+      // lane s takes node s of the gathered ranges: r = ranges ending at or before s
+      int r = 0;
+#pragma unroll
+      for (int b = 16; b > 0; b >>= 1) {
+        const int cand = r + b;
+        const int v = __shfl_sync(0xffffffffu, incl, (cand - 1) & 31);
+        if (cand <= take && v <= lane) r = cand;
+      }
+      // every lane executes the shuffle (a full-mask shuffle reached by only
+      // some lanes is undefined); the value is selected afterwards
+      const int prev = __shfl_sync(0xffffffffu, incl, (r - 1) & 31);
+      const int excl = r > 0 ? prev : 0;
+      const int rfirst = __shfl_sync(0xffffffffu, rfirst_l, r & 31);
+      const uint32_t mask = (uint32_t)__shfl_sync(0xffffffffu, E.y, r & 31);
+      const bool has = lane < total;
+      const int node = has ? rfirst + (lane - excl) : 0;
       if (__any_sync(0xffffffffu, has && (node < 0 || node >= nodes_total))) {
         if (lane == 0) set_status(A.wsb, ST_TREELINK);
         break;
@@ -655,21 +788,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
         if (lane == 0) set_status(A.wsb, ST_TREELINK);
         break;
       }
-      // OPEN internal nodes: push all children with the same lanes
-      const int npush = (cls == CL_OPEN && !leaf) ? nch : 0;
-      int incl = npush;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      for (int c = 0; c < npush; ++c) W.stack[sp + incl - npush + c] = make_int2(ND.z + c, (int)mask);
-      sp += __shfl_sync(0xffffffffu, incl, 31);
+      // OPEN internal nodes: push their child range with the same lanes
+      const bool push = cls == CL_OPEN && !leaf;
+      const uint32_t pm = __ballot_sync(0xffffffffu, push);
+      if (push) W.stack[sp + __popc(pm & lt)] = make_int2((int)((uint32_t)ND.z | ((uint32_t)nch << 28)), (int)mask);
+      sp += __popc(pm);
       // OPEN leaves and ACCEPTed nodes: queue them for evaluation
       const bool q = (cls == CL_OPEN && leaf) || cls == CL_ACCEPT;
       const uint32_t qm = __ballot_sync(0xffffffffu, q);
       if (q) {
-        const int fl = image_flags(A, G, NC);
+        const int fl = image_flags(A, G, NC) | (subgroup_bits(A, W, NC, mask, cls == CL_ACCEPT) << 8);
         W.queue[nq + __popc(qm & lt)] =
             cls == CL_ACCEPT ? make_int4(node, -1, (int)mask, fl) : make_int4(ND.x, ND.y, (int)mask, fl);
       }
@@ -697,23 +825,24 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
         const uint32_t om = __ballot_sync(0xffffffffu, dec == DEC_OPEN);
         const int fl = image_flags(A, G, MC);
         if (am) {
-          if (lane == 0) W.queue[nq] = make_int4(mnode, -1, (int)am, fl);
+          if (lane == 0) W.queue[nq] = make_int4(mnode, -1, (int)am, fl | (subgroup_bits(A, W, MC, am, true) << 8));
           ++nq;
         }
         if (om) {
           if (meta_leaf(MD.w)) {
-            if (lane == 0) W.queue[nq] = make_int4(MD.x, MD.y, (int)om, fl);
+            if (lane == 0)
+              W.queue[nq] = make_int4(MD.x, MD.y, (int)om, fl | (subgroup_bits(A, W, MC, om, false) << 8));
             ++nq;
           } else {
-            const int mch = meta_nchild(MD.w);
-            if (lane < mch) W.stack[sp + lane] = make_int2(MD.z + lane, (int)om);
-            sp += mch;
+            const uint32_t mch = (uint32_t)meta_nchild(MD.w);
+            if (lane == 0) W.stack[sp] = make_int2((int)((uint32_t)MD.z | (mch << 28)), (int)om);
+            ++sp;
           }
         }
       }
       __syncwarp();
     } else if (nq > 0) {
-      L.evaluate(A, W, nq, lane);
+      evaluate_queue(A, W, nq, lane, L);
       nq = 0;
       __syncwarp();
     } else {

@@ -120,3 +120,35 @@ def test_deterministic_repeat():
     a1, t1, c1, _ = forward(w, dev, 0.5)
     a2, t2, c2, _ = forward(w, dev, 0.5)
     assert np.array_equal(a1, a2) and t1 == t2
+
+
+def test_walk_iteration_cap_reports_error():
+    """A walk that exceeds its node-visit cap stops and reports OG_EWALK
+    through the workspace status (no trap, the context stays usable)."""
+    dev = device()
+    m = og()
+    w = ics.make("uniform4096", 2000)
+    from gpu_util import build_tree
+    tree, _, _ = build_tree(w, dev, max_walk_iters=5)
+    with pytest.raises(m.OGError) as e:
+        m.shortrange_accel(tree, w.r_s, 0.5)
+    assert e.value.code == 4
+    # the device is still usable afterwards
+    tree2, _, _ = build_tree(w, dev)
+    acc, tot, _ = m.shortrange_accel(tree2, w.r_s, 0.5)
+    assert tot.item() > 0
+
+
+def test_walk_refuses_a_failed_tree():
+    """A tree whose build ran out of node capacity is flagged; the walk
+    refuses it with OG_ETREE instead of reading it."""
+    dev = device()
+    m = og()
+    w = ics.make("uniform4096", 3000)
+    pos = torch.tensor(w.pos, device=dev)
+    mass = torch.tensor(w.mass, device=dev)
+    keys, order = m.keys_sort(pos, 1.0)
+    tree = m.tree_build(keys, order, pos, mass, 1.0 / 480, 1.0, p=m.params(node_capacity=40), check=False)
+    with pytest.raises(m.OGError) as e:
+        m.shortrange_accel(tree, w.r_s, 0.5)
+    assert e.value.code == 5
