@@ -11,11 +11,14 @@
 // per-particle walk (the rules are listed in og.h), while node data is read
 // once per warp.
 //
-// Evaluation.  Queued entries are expanded into source slots and staged in
-// shared memory 32 at a time.  The warp's lanes form four sub-groups of 8
-// consecutive targets; each sub-group evaluates only the staged sources whose
-// entry can reach its own (smaller) box, so distant halves of a group's
-// interaction list do not cost every lane.
+// Evaluation (FP32).  Queued entries are expanded into source slots and
+// staged in shared memory 32 at a time.  A cheap conservative test (|x_i|^2 +
+// |x_j|^2 - 2 x_i.x_j against r_cut^2, with a per-slot rounding margin) marks
+// the (target, source) pairs that can lie inside the cut; the marked pairs are
+// compacted into a target-major list by a warp prefix sum, and each warp
+// iteration evaluates 32 listed pairs.  Every target then sums its own pair
+// results in slot order, so the result does not depend on which lane
+// evaluated a pair.  The FP64 variant evaluates the staged slots in lockstep.
 //
 // FP32 path.  Positions are split floats in box units (hi a multiple of 2^-23,
 // lo the rest), so hi_i - hi_j is exact and every displacement
@@ -25,13 +28,13 @@
 // reference, so decisions agree with an FP64 walk.  Interactions use the
 // special-function unit (rsqrt, ex2) and a polynomial for
 // erfcx(u) + 2u/sqrt(pi); per-target sums are Kahan-compensated after every
-// batch of 32 staged sources.
+// batch of 32 staged sources (at most 32 terms per target).
 #include "og_internal.cuh"
 #include "short_range_poly.inc"
 
 namespace og {
 
-constexpr int kWarpsPerBlock = 4;
+constexpr int kWarpsPerBlock = 2;
 
 enum : int { DEC_DISCARD = 0, DEC_OPEN = 1, DEC_ACCEPT = 2, DEC_ACCEPT_OUT = 3, DEC_UNSURE = 4 };
 
@@ -181,27 +184,18 @@ constexpr int kStackNeed = 32;   // a step pushes at most one range per popped n
 constexpr int kQueue = 128;      // queued leaves / accepted nodes per warp
 constexpr int kQueueNeed = 64;   // a step queues at most 2 entries per node
 constexpr int kSlots = 32;       // sources staged per evaluation batch
+constexpr int kWin = 64;         // pair results held at once (FP32 evaluation)
 
 // Stack entry: (first node | node count << 28, lane mask); node indices stay
-// below 2^28 (checked on the host).
-// Per-warp views of the block's shared arrays.  Queue entry: (first particle
-// or node, particle count or -1 for an accepted node, lane mask, image flags).
+// below 2^28 (checked on the host).  Queue entry: (first particle or node,
+// particle count or -1 for an accepted node, lane mask, image flags).
 // Image flags bit 0: one shift puts the whole entry at the minimum image of
 // every target of the group (bits 1-6: the shift per axis, 0 / +1 / -1).
 struct WarpBufs {
   int2* stack;
   int4* queue;
   int* qoff;
-  double* slot;          // kSlots x 48 bytes: FP32 (float4 a, float4 b, int4 c) or FP64 (5 doubles + 2 ints)
-  float4* sgbox;         // 4 sub-groups x (lo, hi) boxes of 8 consecutive targets
-  unsigned char* lists;  // 4 sub-groups x kSlots staged-slot indices
 };
-
-// Sub-groups: lanes 8g .. 8g+7 of a warp (8 Hilbert-consecutive targets).
-// A queued entry is evaluated only by the sub-groups whose targets can reach
-// it: its lane mask has bits in the sub-group and (for a leaf) its cube lies
-// within rcut of the sub-group's box.  Queue flags bits 8-11 hold that set.
-constexpr int kSub = 4;
 
 enum : int { CL_NONE = -1, CL_DROP = 0, CL_OPEN = 1, CL_ACCEPT = 2, CL_MIXED = 3 };
 
@@ -259,26 +253,6 @@ __device__ __forceinline__ float shift_of(int flags, int axis) {
   return c == 1 ? 1.0f : (c == 2 ? -1.0f : 0.0f);
 }
 
-__device__ __forceinline__ int subgroup_bits(const WalkArgs& A, const WarpBufs& W, const float4& NC, uint32_t mask,
-                                             bool accepted) {
-  int bits = 0;
-#pragma unroll
-  for (int g = 0; g < kSub; ++g) {
-    if (((mask >> (8 * g)) & 0xffu) == 0u) continue;
-    if (accepted) {
-      bits |= 1 << g;
-      continue;
-    }
-    const float4 lo = W.sgbox[2 * g], hi = W.sgbox[2 * g + 1];
-    const float hs = 0.5f * NC.w;
-    const float gx = fmaxf(fabsf(mi1(NC.x - 0.5f * (lo.x + hi.x))) - 0.5f * (hi.x - lo.x) - hs, 0.f);
-    const float gy = fmaxf(fabsf(mi1(NC.y - 0.5f * (lo.y + hi.y))) - 0.5f * (hi.y - lo.y) - hs, 0.f);
-    const float gz = fmaxf(fabsf(mi1(NC.z - 0.5f * (lo.z + hi.z))) - 0.5f * (hi.z - lo.z) - hs, 0.f);
-    if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= A.grp_rc2) bits |= 1 << g;
-  }
-  return bits;
-}
-
 // Validates the queue and writes the slot offsets; returns the slot count or
 // -1 if an entry is malformed (then nothing may be evaluated).
 __device__ __forceinline__ int queue_offsets(const WalkArgs& A, const WarpBufs& W, int nq, int lane) {
@@ -321,21 +295,48 @@ __device__ __forceinline__ int entry_of(const WarpBufs& W, int nq, int s) {
   return lo;
 }
 
+// 32 x 32 bit-matrix transpose across the warp: lane r holds row r (bit c =
+// column c) and receives column r.  Five stages swap the off-diagonal blocks
+// of side 16, 8, 4, 2, 1 between partner lanes.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+  const uint32_t keep[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+  int j = 16;
+#pragma unroll
+  for (int st = 0; st < 5; ++st, j >>= 1) {
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) == 0 ? ((x & keep[st]) | ((y & keep[st]) << j)) : ((x & ~keep[st]) | ((y & ~keep[st]) >> j));
+  }
+  return x;
+}
+
 // ------------------------------------------------------------------ lanes
 
 // FP32 lane: forward (ADJ = false) or adjoint (ADJ = true).
 template <bool ADJ>
 struct LaneF32 {
+  struct Smem {
+    float4 sa[kSlots];    // staged source: hi part (image-shifted), mass
+    float4 sb[kSlots];    // lo part, h^2
+    float4 sf[kSlots];    // filter form: -2 x, -2 y, -2 z, |x|^2 - margin (relative to the group centre)
+    int4 sc[kSlots];      // id (particle, or -2 - node), per-pair image flag, cut band lo / hi (float bits)
+    float4 tA[kGroup];    // targets: hi part, h^2
+    float4 tB[kGroup];    // targets: lo part
+    float4 tW[ADJ ? kGroup : 1];   // adjoint: dL/da of each target
+    float4 sG[ADJ ? kSlots : 1];   // adjoint: source-side sums of the batch (G, S) per slot
+    float4 F[kWin];       // pair results of the current window (target side, hit flag)
+    int self[kGroup];     // staged slot holding the target itself, or -1
+    unsigned short list[kSlots * kGroup];  // pair list (target << 5 | slot), target-major
+  };
+
   int64_t k;          // sorted index of this lane's target
   bool valid;
   float xh[3], xl[3]; // split position
-  float h2;           // own softening support squared (box units)
+  float xr[3], sr;    // position relative to the group centre and its square (filter)
   float P[3];         // partial sum since the last fold
   float S[3], C[3];   // Kahan total and compensation
-  float w[3];         // adjoint weight
   int nint;
 
-  __device__ void init(const WalkArgs& A, int64_t kk, bool v) {
+  __device__ void init(const WalkArgs& A, Smem& M, int64_t kk, bool v, int lane, const GroupInfo& G) {
     k = kk;
     valid = v;
     const int64_t kc = v ? kk : 0;  // never form an out-of-range address
@@ -343,19 +344,28 @@ struct LaneF32 {
     const float4 b = A.T.pB[kc];
     xh[0] = a.x; xh[1] = a.y; xh[2] = a.z;
     xl[0] = b.x; xl[1] = b.y; xl[2] = b.z;
-    h2 = b.w;
+    M.tA[lane] = make_float4(a.x, a.y, a.z, b.w);
+    M.tB[lane] = make_float4(b.x, b.y, b.z, 0.f);
+    xr[0] = (a.x - G.cx) + b.x;
+    xr[1] = (a.y - G.cy) + b.y;
+    xr[2] = (a.z - G.cz) + b.z;
+    sr = fmaf(xr[0], xr[0], fmaf(xr[1], xr[1], xr[2] * xr[2]));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { P[c] = 0.f; S[c] = 0.f; C[c] = 0.f; w[c] = 0.f; }
-    if (ADJ && v) {
-      const int32_t i = A.T.order[kk];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) w[c] = A.w[3 * (int64_t)i + c];
+    for (int c = 0; c < 3; ++c) { P[c] = 0.f; S[c] = 0.f; C[c] = 0.f; }
+    if (ADJ) {
+      float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (v) {
+        const int32_t i = A.T.order[kk];
+        w = make_float4(A.w[3 * (int64_t)i], A.w[3 * (int64_t)i + 1], A.w[3 * (int64_t)i + 2], 0.f);
+      }
+      M.tW[lane] = w;
     }
     nint = 0;
   }
 
   // Exact per-lane decision for a node (FP32 with an FP64 re-check in the band).
-  __device__ int decide(const WalkArgs& A, int node, const int4& ND, const float4& NC) {
+  __device__ int decide(const WalkArgs& A, int node, const int4& ND, const float4& NC, const float4& NA,
+                        const float4& NB) {
     const float s = NC.w, hs = 0.5f * s;
     // hi differences are exact: the minimum image is taken before the lo parts are added
     const float ax = fabsf(mi1(NC.x - xh[0]) - xl[0]);
@@ -364,8 +374,6 @@ struct LaneF32 {
     const float ex = fmaxf(ax - hs, 0.f), ey = fmaxf(ay - hs, 0.f), ez = fmaxf(az - hs, 0.f);
     const float e2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
     if (e2 > A.rc2_hi) return DEC_DISCARD;
-    const float4 NA = A.T.nA[node];
-    const float4 NB = A.T.nB[node];
     const float d0 = mi1(xh[0] - NA.x) + (xl[0] - NB.x);
     const float d1 = mi1(xh[1] - NA.y) + (xl[1] - NB.y);
     const float dz = mi1(xh[2] - NA.z) + (xl[2] - NB.z);
@@ -389,15 +397,17 @@ struct LaneF32 {
     return dec;
   }
 
-  // Stage slot s of the queue into batch position `lane`; returns the
-  // sub-groups that evaluate it.
-  __device__ __forceinline__ int stage(const WalkArgs& A, const WarpBufs& W, int nq, int s, int lane) {
+  // Stage slot s of the queue into batch position `lane`; returns the lane
+  // mask of its queue entry.
+  __device__ __forceinline__ uint32_t stage(const WalkArgs& A, const WarpBufs& W, Smem& M, int nq, int s, int lane,
+                                            const GroupInfo& G, int64_t gbase, float Rg) {
     const int e = entry_of(W, nq, s);
     const int4 Q = W.queue[e];
     float4 a, b;
     int id;
     float lo, hi;
-    if (Q.y < 0) {
+    const bool node = Q.y < 0;
+    if (node) {
       a = A.T.nA[Q.x];
       b = A.T.nB[Q.x];
       id = -2 - Q.x;
@@ -410,18 +420,27 @@ struct LaneF32 {
       lo = A.pp_lo;
       hi = A.pp_hi;
     }
-    if (Q.w & 1) {
+    const bool uni = (Q.w & 1) != 0;
+    if (uni) {
       a.x -= shift_of(Q.w, 0);
       a.y -= shift_of(Q.w, 1);
       a.z -= shift_of(Q.w, 2);
-    } else {
-      b.w = -b.w;  // negative h^2 marks "minimum image per pair"
     }
-    float4* f = reinterpret_cast<float4*>(W.slot) + 3 * lane;
-    f[0] = a;
-    f[1] = b;
-    reinterpret_cast<int4*>(f)[2] = make_int4(id, Q.z, __float_as_int(lo), __float_as_int(hi));
-    return (Q.w >> 8) & 0xf;
+    float4 f = make_float4(0.f, 0.f, 0.f, -1e30f);  // always a candidate
+    if (uni && !node) {
+      // conservative margin: the FP32 evaluation of |x_i - x_j|^2 below is
+      // within 18 u (|x_i| + |x_j|)^2 of the exact value (u = 2^-24)
+      const float x0 = (a.x - G.cx) + b.x, x1 = (a.y - G.cy) + b.y, x2 = (a.z - G.cz) + b.z;
+      const float sj = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
+      const float rr = sqrtf(sj) + Rg;
+      f = make_float4(-2.f * x0, -2.f * x1, -2.f * x2, sj - 3.814697265625e-06f * rr * rr);
+    }
+    M.sa[lane] = a;
+    M.sb[lane] = b;
+    M.sf[lane] = f;
+    M.sc[lane] = make_int4(id, uni ? 0 : 1, __float_as_int(lo), __float_as_int(hi));
+    if (id >= gbase && id < gbase + kGroup) M.self[id - gbase] = lane;
+    return (uint32_t)Q.z;
   }
 
   __device__ __forceinline__ void fold() {
@@ -432,69 +451,131 @@ struct LaneF32 {
     }
   }
 
-  // One (target, staged source) pair; `has` is false for idle lanes.  In the
-  // adjoint the source-side terms are summed over the lanes of the sub-group
-  // (all of which hold the same slot) and added once.
-  __device__ __forceinline__ void pair(const WalkArgs& A, const WarpBufs& W, int t, bool has, int lane) {
-    const float4* f = reinterpret_cast<const float4*>(W.slot);
-    const float4 a = f[3 * t];
-    const float4 b = f[3 * t + 1];
-    const int4 c = reinterpret_cast<const int4*>(f)[3 * t + 2];
-    float dh0 = xh[0] - a.x, dh1 = xh[1] - a.y, dh2 = xh[2] - a.z;
-    if (b.w < 0.0f) {
+  // Target i of the group against staged slot s: the exact cut decision, and
+  // the interaction (target-side term, hit flag).  In the adjoint the
+  // source-side terms are added to the slot's shared sums.
+  __device__ __forceinline__ float4 pair_eval(const WalkArgs& A, Smem& M, int i, int s, int64_t gbase) {
+    const float4 ta = M.tA[i], tb = M.tB[i];
+    const float4 a = M.sa[s], b = M.sb[s];
+    const int4 c = M.sc[s];
+    float dh0 = ta.x - a.x, dh1 = ta.y - a.y, dh2 = ta.z - a.z;
+    if (c.y) {
       dh0 = mi1(dh0);
       dh1 = mi1(dh1);
       dh2 = mi1(dh2);
     }
     float dv[3];
-    dv[0] = dh0 + (xl[0] - b.x);
-    dv[1] = dh1 + (xl[1] - b.y);
-    dv[2] = dh2 + (xl[2] - b.z);
+    dv[0] = dh0 + (tb.x - b.x);
+    dv[1] = dh1 + (tb.y - b.y);
+    dv[2] = dh2 + (tb.z - b.z);
     const float r2 = fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2]));
-    bool hit = has && valid && ((c.y >> lane) & 1) && c.x != k;
-    if (hit && !(r2 < __int_as_float(c.z)))
-      hit = c.x >= 0 && r2 <= __int_as_float(c.w) && pair_inside_exact(A, k, c.x);
-    float jw[3] = {0.f, 0.f, 0.f}, wg = 0.f;
-    if (hit) {
-      float F, Fr;
-      force_f32<ADJ>(A, r2, fmaxf(h2, fabsf(b.w)), F, Fr);
-      if (!ADJ) {
-        const float sc = -a.w * F;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) P[q] = fmaf(sc, dv[q], P[q]);
-      } else {
-        const float dw = fmaf(dv[0], w[0], fmaf(dv[1], w[1], dv[2] * w[2]));
-        const float qq = Fr * dw;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          jw[q] = -fmaf(F, w[q], qq * dv[q]);
-          P[q] = fmaf(a.w, jw[q], P[q]);
-        }
-        wg = -F * dw;
-      }
-      ++nint;
+    bool in = r2 < __int_as_float(c.z);
+    if (!in) in = c.x >= 0 && r2 <= __int_as_float(c.w) && pair_inside_exact(A, gbase + i, c.x);
+    if (!in) return make_float4(0.f, 0.f, 0.f, 0.f);
+    float F, Fr;
+    force_f32<ADJ>(A, r2, fmaxf(ta.w, b.w), F, Fr);
+    if (!ADJ) {
+      const float sc = -a.w * F;
+      return make_float4(sc * dv[0], sc * dv[1], sc * dv[2], 1.f);
+    } else {
+      const float4 w = M.tW[i];
+      const float dw = fmaf(dv[0], w.x, fmaf(dv[1], w.y, dv[2] * w.z));
+      const float qq = Fr * dw;
+      const float j0 = -fmaf(F, w.x, qq * dv[0]);
+      const float j1 = -fmaf(F, w.y, qq * dv[1]);
+      const float j2 = -fmaf(F, w.z, qq * dv[2]);
+      atomicAdd(&M.sG[s].x, j0);
+      atomicAdd(&M.sG[s].y, j1);
+      atomicAdd(&M.sG[s].z, j2);
+      atomicAdd(&M.sG[s].w, -F * dw);
+      return make_float4(a.w * j0, a.w * j1, a.w * j2, 1.f);
     }
-    if (ADJ) {
-      const uint32_t hm = __ballot_sync(0xffffffffu, hit);
-      if (hm) {
-        float g0 = jw[0], g1 = jw[1], g2 = jw[2], sg = wg;
+  }
+
+  // Evaluate the queued entries (see the header comment).
+  __device__ void evaluate(const WalkArgs& A, const WarpBufs& W, Smem& M, int nq, int lane, const GroupInfo& G,
+                           int64_t gbase, uint32_t vmask, float Rg) {
+    const int total = queue_offsets(A, W, nq, lane);
+    if (total < 0) {
+      if (lane == 0) set_status(A.wsb, ST_TREELINK);
+      return;
+    }
+    for (int base = 0; base < total; base += kSlots) {
+      const int cnt = min(kSlots, total - base);
+      M.self[lane] = -1;
+      if (ADJ) M.sG[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncwarp();
+      uint32_t q = 0;
+      if (lane < cnt) q = stage(A, W, M, nq, base + lane, lane, G, gbase, Rg);
+      __syncwarp();
+      // bit s of msk: slot s is in this lane's part of its entry's lane mask
+      const uint32_t cm = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
+      uint32_t msk;
+      if (__any_sync(0xffffffffu, lane < cnt && q != vmask)) msk = transpose32(q, lane);
+      else msk = valid ? cm : 0u;
+      // conservative cut test for every staged slot
+      uint32_t hit = 0;
+#pragma unroll 8
+      for (int s = 0; s < cnt; ++s) {
+        const float4 f = M.sf[s];
+        const float r2 = fmaf(f.x, xr[0], fmaf(f.y, xr[1], fmaf(f.z, xr[2], f.w + sr)));
+        hit |= (r2 < A.rc2_hi ? 1u : 0u) << s;
+      }
+      hit &= msk;
+      const int so = M.self[lane];
+      if (so >= 0) hit &= ~(1u << so);
+      // compaction: target-major pair list
+      const int c = __popc(hit);
+      int incl = c;
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-          g0 += __shfl_xor_sync(0xffffffffu, g0, o);
-          g1 += __shfl_xor_sync(0xffffffffu, g1, o);
-          g2 += __shfl_xor_sync(0xffffffffu, g2, o);
-          sg += __shfl_xor_sync(0xffffffffu, sg, o);
-        }
-        const uint32_t seg = (hm >> (lane & 24)) & 0xffu;
-        if (seg && (lane & 7) == __ffs(seg) - 1) {
-          double* G = c.x >= 0 ? A.Gp + 3 * (int64_t)c.x : A.Gn + 3 * (int64_t)(-2 - c.x);
-          double* Sx = c.x >= 0 ? A.Sp + c.x : A.Sn + (-2 - c.x);
-          atomicAdd(G, f2d_exact(g0));
-          atomicAdd(G + 1, f2d_exact(g1));
-          atomicAdd(G + 2, f2d_exact(g2));
-          atomicAdd(Sx, f2d_exact(sg));
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int T = __shfl_sync(0xffffffffu, incl, 31);
+      const int off = incl - c;
+      {
+        uint32_t m = hit;
+        int t = off;
+        while (m) {
+          const int s = __ffs(m) - 1;
+          m &= m - 1;
+          M.list[t++] = (unsigned short)((lane << 5) | s);
         }
       }
+      __syncwarp();
+      for (int wb = 0; wb < T; wb += kWin) {
+        const int we = min(T, wb + kWin);
+        for (int p = wb + lane; p < we; p += 32) {
+          const int e = M.list[p];
+          M.F[p - wb] = pair_eval(A, M, e >> 5, e & 31, gbase);
+        }
+        __syncwarp();
+        // each target sums its own results in slot order
+        const int lo = max(off, wb), hi = min(off + c, we);
+        for (int t = lo; t < hi; ++t) {
+          const float4 v = M.F[t - wb];
+          P[0] += v.x;
+          P[1] += v.y;
+          P[2] += v.z;
+          nint += (int)v.w;
+        }
+        __syncwarp();
+      }
+      fold();
+      if (ADJ && lane < cnt) {
+        const float4 g = M.sG[lane];
+        if (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f) {
+          const int id = M.sc[lane].x;
+          double* Gd = id >= 0 ? A.Gp + 3 * (int64_t)id : A.Gn + 3 * (int64_t)(-2 - id);
+          double* Sd = id >= 0 ? A.Sp + id : A.Sn + (-2 - id);
+          atomicAdd(Gd, f2d_exact(g.x));
+          atomicAdd(Gd + 1, f2d_exact(g.y));
+          atomicAdd(Gd + 2, f2d_exact(g.z));
+          atomicAdd(Sd, f2d_exact(g.w));
+        }
+      }
+      __syncwarp();
     }
   }
 
@@ -513,8 +594,13 @@ struct LaneF32 {
 };
 
 // FP64 lane (forward only): the same traversal and decisions, double-precision
-// interactions with the library's erfc / exp, plain double sums.
+// interactions with the library's erfc / exp, plain double sums; every lane
+// evaluates every staged slot in lockstep.
 struct LaneF64 {
+  struct Smem {
+    double slot[kSlots * 6];  // per slot: double x, y, z, m, h; int id, int lane mask
+  };
+
   int64_t k;
   bool valid;
   double x[3];
@@ -522,7 +608,7 @@ struct LaneF64 {
   double a[3];
   int nint;
 
-  __device__ void init(const WalkArgs& A, int64_t kk, bool v) {
+  __device__ void init(const WalkArgs& A, Smem&, int64_t kk, bool v, int, const GroupInfo&) {
     k = kk;
     valid = v;
     const int64_t kc = v ? kk : 0;
@@ -535,15 +621,14 @@ struct LaneF64 {
     nint = 0;
   }
 
-  __device__ int decide(const WalkArgs& A, int node, const int4& ND, const float4&) {
+  __device__ int decide(const WalkArgs& A, int node, const int4& ND, const float4&, const float4&, const float4&) {
     return decide_exact(A, k, node, meta_level(ND.w));
   }
 
-  // Slot layout (48 bytes): double x, y, z, m, h; int id, int mask.
-  __device__ __forceinline__ int stage(const WalkArgs& A, const WarpBufs& W, int nq, int s, int lane) {
+  __device__ __forceinline__ void stage(const WalkArgs& A, const WarpBufs& W, Smem& M, int nq, int s, int lane) {
     const int e = entry_of(W, nq, s);
     const int4 Q = W.queue[e];
-    double* d = W.slot + 6 * lane;
+    double* d = M.slot + 6 * lane;
     int* ii = reinterpret_cast<int*>(d + 5);
     if (Q.y < 0) {
       const int n = Q.x;
@@ -563,16 +648,13 @@ struct LaneF64 {
       ii[0] = j;
     }
     ii[1] = Q.z;
-    return (Q.w >> 8) & 0xf;
   }
 
-  __device__ __forceinline__ void fold() {}
-
-  __device__ __forceinline__ void pair(const WalkArgs& A, const WarpBufs& W, int t, bool has, int lane) {
-    const double* d = W.slot + 6 * t;
+  __device__ __forceinline__ void pair(const WalkArgs& A, const Smem& M, int t, int lane) {
+    const double* d = M.slot + 6 * t;
     const int* ii = reinterpret_cast<const int*>(d + 5);
     const int id = ii[0];
-    const bool mine = has && valid && ((ii[1] >> lane) & 1) && id != k;
+    const bool mine = valid && ((ii[1] >> lane) & 1) && id != k;
     if (!mine) return;
     double dv[3];
 #pragma unroll
@@ -598,6 +680,22 @@ struct LaneF64 {
     ++nint;
   }
 
+  __device__ void evaluate(const WalkArgs& A, const WarpBufs& W, Smem& M, int nq, int lane, const GroupInfo&,
+                           int64_t, uint32_t, float) {
+    const int total = queue_offsets(A, W, nq, lane);
+    if (total < 0) {
+      if (lane == 0) set_status(A.wsb, ST_TREELINK);
+      return;
+    }
+    for (int base = 0; base < total; base += kSlots) {
+      const int cnt = min(kSlots, total - base);
+      if (lane < cnt) stage(A, W, M, nq, base + lane, lane);
+      __syncwarp();
+      for (int t = 0; t < cnt; ++t) pair(A, M, t, lane);
+      __syncwarp();
+    }
+  }
+
   __device__ void finish(const WalkArgs& A) {
     if (!valid) return;
     const int32_t i = A.T.order[k];
@@ -607,44 +705,6 @@ struct LaneF64 {
   }
 };
 
-// ------------------------------------------------------------------ evaluation
-
-// Evaluate the queued entries: stage 32 sources at a time; each sub-group
-// walks the list of staged sources that can reach it.
-template <class Lane>
-__device__ __forceinline__ void evaluate_queue(const WalkArgs& A, const WarpBufs& W, int nq, int lane, Lane& L) {
-  const int total = queue_offsets(A, W, nq, lane);
-  if (total < 0) {
-    if (lane == 0) set_status(A.wsb, ST_TREELINK);
-    return;
-  }
-  const int sg = lane >> 3;
-  const uint32_t lt = (1u << lane) - 1u;
-  for (int base = 0; base < total; base += kSlots) {
-    const int cnt = min(kSlots, total - base);
-    int bits = 0;
-    if (lane < cnt) bits = L.stage(A, W, nq, base + lane, lane);
-    int my_n = 0, iters = 0;
-#pragma unroll
-    for (int g = 0; g < kSub; ++g) {
-      const bool in = ((bits >> g) & 1) != 0;
-      const uint32_t m = __ballot_sync(0xffffffffu, in);
-      if (in) W.lists[g * kSlots + __popc(m & lt)] = (unsigned char)lane;
-      const int ng = __popc(m);
-      if (g == sg) my_n = ng;
-      iters = max(iters, ng);
-    }
-    __syncwarp();
-    for (int t = 0; t < iters; ++t) {
-      const bool has = t < my_n;
-      const int slot = has ? (int)W.lists[sg * kSlots + t] : 0;
-      L.pair(A, W, slot, has, lane);
-    }
-    L.fold();
-    __syncwarp();
-  }
-}
-
 // ------------------------------------------------------------------ traversal
 
 template <class Lane>
@@ -652,9 +712,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   __shared__ int2 s_stack[kWarpsPerBlock][kStack];
   __shared__ int4 s_queue[kWarpsPerBlock][kQueue];
   __shared__ int s_qoff[kWarpsPerBlock][kQueue + 1];
-  __shared__ __align__(16) double s_slot[kWarpsPerBlock][kSlots * 6];
-  __shared__ float4 s_sgbox[kWarpsPerBlock][2 * kSub];
-  __shared__ unsigned char s_lists[kWarpsPerBlock][kSub * kSlots];
+  __shared__ typename Lane::Smem s_lane[kWarpsPerBlock];
   const TreeDev& T = A.T;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t g = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
@@ -667,14 +725,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   W.stack = s_stack[wib];
   W.queue = s_queue[wib];
   W.qoff = s_qoff[wib];
-  W.slot = s_slot[wib];
-  W.sgbox = s_sgbox[wib];
-  W.lists = s_lists[wib];
+  typename Lane::Smem& M = s_lane[wib];
   int nodes_total = 0;
   for (int l = 0; l < kLevels; ++l) nodes_total += T.sb->level_cnt[l];
   if (nodes_total > T.cap) nodes_total = (int)T.cap;
 
-  const int64_t k = g * kGroup + lane;
+  const int64_t gbase = g * kGroup;
+  const int64_t k = gbase + lane;
   const bool valid = k < T.n;
   const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
   const uint32_t lt = (1u << lane) - 1u;
@@ -687,32 +744,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
     G.ey = 0.5f * (hi.y - lo.y) * 1.0001f + 1e-7f;
     G.ez = 0.5f * (hi.z - lo.z) * 1.0001f + 1e-7f;
   }
+  // bound on |x_i - group centre| for the evaluation's cut filter
+  const float Rg = sqrtf(fmaf(G.ex, G.ex, fmaf(G.ey, G.ey, G.ez * G.ez))) * 1.0001f + 1e-6f;
 
   Lane L;
-  L.init(A, k, valid);
-
-  {
-    // bounding box of each sub-group of 8 targets (box units, padded outward)
-    const float4 pa = T.pA[valid ? k : 0], pb = T.pB[valid ? k : 0];
-    float lo[3] = {pa.x + pb.x, pa.y + pb.y, pa.z + pb.z};
-    float hi[3] = {lo[0], lo[1], lo[2]};
-    if (!valid) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) { lo[c] = 1e30f; hi[c] = -1e30f; }
-    }
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
-        hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
-      }
-    if ((lane & 7) == 0) {
-      const float pad = 2e-7f;
-      W.sgbox[2 * (lane >> 3)] = make_float4(lo[0] - pad, lo[1] - pad, lo[2] - pad, 0.f);
-      W.sgbox[2 * (lane >> 3) + 1] = make_float4(hi[0] + pad, hi[1] + pad, hi[2] + pad, 0.f);
-    }
-  }
+  L.init(A, M, k, valid, lane, G);
 
   if (lane == 0) W.stack[0] = make_int2((int)(1u << 28), (int)vmask);  // the root: node 0, one node
   int sp = 1, nq = 0;
@@ -797,12 +833,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
       const bool q = (cls == CL_OPEN && leaf) || cls == CL_ACCEPT;
       const uint32_t qm = __ballot_sync(0xffffffffu, q);
       if (q) {
-        const int fl = image_flags(A, G, NC) | (subgroup_bits(A, W, NC, mask, cls == CL_ACCEPT) << 8);
+        const int fl = image_flags(A, G, NC);
         W.queue[nq + __popc(qm & lt)] =
             cls == CL_ACCEPT ? make_int4(node, -1, (int)mask, fl) : make_int4(ND.x, ND.y, (int)mask, fl);
       }
       nq += __popc(qm);
-      // MIXED nodes: exact per-lane decisions, one node at a time
+      // MIXED nodes: exact per-lane decisions, one node at a time; the node's
+      // data comes from the lane that loaded it
       uint32_t mm = __ballot_sync(0xffffffffu, cls == CL_MIXED);
       while (mm) {
         const int src = __ffs(mm) - 1;
@@ -814,24 +851,31 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
         MD.y = __shfl_sync(0xffffffffu, ND.y, src);
         MD.z = __shfl_sync(0xffffffffu, ND.z, src);
         MD.w = __shfl_sync(0xffffffffu, ND.w, src);
-        float4 MC;
+        float4 MC, MA, MB;
         MC.x = __shfl_sync(0xffffffffu, NC.x, src);
         MC.y = __shfl_sync(0xffffffffu, NC.y, src);
         MC.z = __shfl_sync(0xffffffffu, NC.z, src);
         MC.w = __shfl_sync(0xffffffffu, NC.w, src);
+        MA.x = __shfl_sync(0xffffffffu, NA.x, src);
+        MA.y = __shfl_sync(0xffffffffu, NA.y, src);
+        MA.z = __shfl_sync(0xffffffffu, NA.z, src);
+        MA.w = __shfl_sync(0xffffffffu, NA.w, src);
+        MB.x = __shfl_sync(0xffffffffu, NB.x, src);
+        MB.y = __shfl_sync(0xffffffffu, NB.y, src);
+        MB.z = __shfl_sync(0xffffffffu, NB.z, src);
+        MB.w = __shfl_sync(0xffffffffu, NB.w, src);
         const bool act = valid && ((mmask >> lane) & 1u);
-        const int dec = act ? L.decide(A, mnode, MD, MC) : DEC_DISCARD;
+        const int dec = act ? L.decide(A, mnode, MD, MC, MA, MB) : DEC_DISCARD;
         const uint32_t am = __ballot_sync(0xffffffffu, dec == DEC_ACCEPT);
         const uint32_t om = __ballot_sync(0xffffffffu, dec == DEC_OPEN);
         const int fl = image_flags(A, G, MC);
         if (am) {
-          if (lane == 0) W.queue[nq] = make_int4(mnode, -1, (int)am, fl | (subgroup_bits(A, W, MC, am, true) << 8));
+          if (lane == 0) W.queue[nq] = make_int4(mnode, -1, (int)am, fl);
           ++nq;
         }
         if (om) {
           if (meta_leaf(MD.w)) {
-            if (lane == 0)
-              W.queue[nq] = make_int4(MD.x, MD.y, (int)om, fl | (subgroup_bits(A, W, MC, om, false) << 8));
+            if (lane == 0) W.queue[nq] = make_int4(MD.x, MD.y, (int)om, fl);
             ++nq;
           } else {
             const uint32_t mch = (uint32_t)meta_nchild(MD.w);
@@ -842,7 +886,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
       }
       __syncwarp();
     } else if (nq > 0) {
-      evaluate_queue(A, W, nq, lane, L);
+      L.evaluate(A, W, M, nq, lane, G, gbase, vmask, Rg);
       nq = 0;
       __syncwarp();
     } else {
