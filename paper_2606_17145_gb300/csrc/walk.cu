@@ -179,12 +179,19 @@ struct GroupInfo {
 
 // ------------------------------------------------------------------ per-warp shared buffers
 
-constexpr int kStack = 704;      // child-range entries per warp: >= 31 x 21 levels + one step
-constexpr int kStackNeed = 32;   // a step pushes at most one range per popped node
+// Traversal stack of child ranges.  A step pops ranges holding up to 32
+// nodes and pushes at most one range per popped node (net growth <= 31).
+// Above kDeep entries a step pops a single range (<= 8 nodes, growth <= 7
+// per level), so the depth stays below kDeep + 31 + 7 x 20 + 8 for any tree.
+constexpr int kStack = 320;
+constexpr int kStackNeed = 32;   // pushes of one step
+constexpr int kDeep = 96;
+static_assert(kDeep + 31 + 7 * 20 + 8 <= kStack - kStackNeed, "stack bound");
 constexpr int kQueue = 128;      // queued leaves / accepted nodes per warp
 constexpr int kQueueNeed = 64;   // a step queues at most 2 entries per node
 constexpr int kSlots = 32;       // sources staged per evaluation batch
 constexpr int kWin = 64;         // pair results held at once (FP32 evaluation)
+constexpr int kList = kSlots * kGroup;  // (node or slot, target) list entries
 
 // Stack entry: (first node | node count << 28, lane mask); node indices stay
 // below 2^28 (checked on the host).  Queue entry: (first particle or node,
@@ -195,6 +202,15 @@ struct WarpBufs {
   int2* stack;
   int4* queue;
   int* qoff;
+  unsigned short* list;  // per-lane decision list (traversal) or pair list (evaluation)
+};
+
+// Nodes of one traversal step that need per-lane decisions.
+struct MixedScratch {
+  int4 D[kGroup];
+  float4 C[kGroup], A[kGroup], B[kGroup];
+  int node[kGroup];
+  uint32_t mask[kGroup], acc[kGroup], open[kGroup];
 };
 
 enum : int { CL_NONE = -1, CL_DROP = 0, CL_OPEN = 1, CL_ACCEPT = 2, CL_MIXED = 3 };
@@ -311,26 +327,85 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 
 // ------------------------------------------------------------------ lanes
 
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Exact per-target decision for a node (FP32 with an FP64 re-check in the
+// band), target given by its split position.
+__device__ __forceinline__ int decide_f32(const WalkArgs& A, int64_t k, const float4& th, const float4& tl, int node,
+                                          const int4& ND, const float4& NC, const float4& NA, const float4& NB) {
+  const float s = NC.w, hs = 0.5f * s;
+  // hi differences are exact: the minimum image is taken before the lo parts are added
+  const float ax = fabsf(mi1(NC.x - th.x) - tl.x);
+  const float ay = fabsf(mi1(NC.y - th.y) - tl.y);
+  const float az = fabsf(mi1(NC.z - th.z) - tl.z);
+  const float ex = fmaxf(ax - hs, 0.f), ey = fmaxf(ay - hs, 0.f), ez = fmaxf(az - hs, 0.f);
+  const float e2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+  if (e2 > A.rc2_hi) return DEC_DISCARD;
+  const float d0 = mi1(th.x - NA.x) + (tl.x - NB.x);
+  const float d1 = mi1(th.y - NA.y) + (tl.y - NB.y);
+  const float dz = mi1(th.z - NA.z) + (tl.z - NB.z);
+  const float d2 = fmaf(d0, d0, fmaf(d1, d1, dz * dz));
+  int dec;
+  if (e2 >= A.rc2_lo) {
+    dec = DEC_UNSURE;
+  } else {
+    const float fx = ax + hs, fy = ay + hs, fz = az + hs;
+    const float far2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+    const float lhs = s * s;
+    const float cmax = fmaxf(ax, fmaxf(ay, az));
+    const int a1 = lhs < A.th2_lo * d2 ? 1 : (lhs > A.th2_hi * d2 ? 0 : 2);
+    const int a2 = cmax > A.lim_hi * s ? 1 : (cmax < A.lim_lo * s ? 0 : 2);
+    const int a3 = far2 < A.rc2_lo ? 1 : (far2 > A.rc2_hi ? 0 : 2);
+    if (a1 == 0 || a2 == 0 || a3 == 0) dec = DEC_OPEN;
+    else if (a1 == 2 || a2 == 2 || a3 == 2) dec = DEC_UNSURE;
+    else dec = d2 < A.rc2_lo ? DEC_ACCEPT : (d2 > A.rc2_hi ? DEC_ACCEPT_OUT : DEC_UNSURE);
+  }
+  if (dec == DEC_UNSURE) dec = decide_exact(A, k, node, meta_level(ND.w));
+  return dec;
+}
+
 // FP32 lane: forward (ADJ = false) or adjoint (ADJ = true).
 template <bool ADJ>
 struct LaneF32 {
+  // per-warp data that lives through the whole walk
   struct Smem {
-    float4 sa[kSlots];    // staged source: hi part (image-shifted), mass
-    float4 sb[kSlots];    // lo part, h^2
-    float4 sf[kSlots];    // filter form: -2 x, -2 y, -2 z, |x|^2 - margin (relative to the group centre)
-    int4 sc[kSlots];      // id (particle, or -2 - node), per-pair image flag, cut band lo / hi (float bits)
     float4 tA[kGroup];    // targets: hi part, h^2
     float4 tB[kGroup];    // targets: lo part
     float4 tW[ADJ ? kGroup : 1];   // adjoint: dL/da of each target
     float4 sG[ADJ ? kSlots : 1];   // adjoint: source-side sums of the batch (G, S) per slot
-    float4 F[kWin];       // pair results of the current window (target side, hit flag)
     int self[kGroup];     // staged slot holding the target itself, or -1
-    unsigned short list[kSlots * kGroup];  // pair list (target << 5 | slot), target-major
+  };
+  // per-batch staging (dead between evaluations; shares memory with the
+  // traversal's scratch)
+  struct Stage {
+    float4 sa[kSlots];    // staged source: hi part (image-shifted), mass
+    float4 sb[kSlots];    // lo part, h^2
+    int4 sc[kSlots];      // id (particle, or -2 - node), per-pair image flag, cut band lo / hi (float bits)
+    float fX[kSlots], fY[kSlots], fZ[kSlots], fW[kSlots];  // filter form (see stage)
+    float4 F[kWin];       // pair results of the current window (target side, hit flag)
+  };
+  // a slot's source, fetched one batch ahead
+  struct Fetch {
+    float4 a, b;
+    int id, flags;
+    uint32_t q;
+    bool node;
   };
 
   int64_t k;          // sorted index of this lane's target
   bool valid;
-  float xh[3], xl[3]; // split position
   float xr[3], sr;    // position relative to the group centre and its square (filter)
   float P[3];         // partial sum since the last fold
   float S[3], C[3];   // Kahan total and compensation
@@ -342,8 +417,6 @@ struct LaneF32 {
     const int64_t kc = v ? kk : 0;  // never form an out-of-range address
     const float4 a = A.T.pA[kc];
     const float4 b = A.T.pB[kc];
-    xh[0] = a.x; xh[1] = a.y; xh[2] = a.z;
-    xl[0] = b.x; xl[1] = b.y; xl[2] = b.z;
     M.tA[lane] = make_float4(a.x, a.y, a.z, b.w);
     M.tB[lane] = make_float4(b.x, b.y, b.z, 0.f);
     xr[0] = (a.x - G.cx) + b.x;
@@ -363,84 +436,72 @@ struct LaneF32 {
     nint = 0;
   }
 
-  // Exact per-lane decision for a node (FP32 with an FP64 re-check in the band).
-  __device__ int decide(const WalkArgs& A, int node, const int4& ND, const float4& NC, const float4& NA,
-                        const float4& NB) {
-    const float s = NC.w, hs = 0.5f * s;
-    // hi differences are exact: the minimum image is taken before the lo parts are added
-    const float ax = fabsf(mi1(NC.x - xh[0]) - xl[0]);
-    const float ay = fabsf(mi1(NC.y - xh[1]) - xl[1]);
-    const float az = fabsf(mi1(NC.z - xh[2]) - xl[2]);
-    const float ex = fmaxf(ax - hs, 0.f), ey = fmaxf(ay - hs, 0.f), ez = fmaxf(az - hs, 0.f);
-    const float e2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-    if (e2 > A.rc2_hi) return DEC_DISCARD;
-    const float d0 = mi1(xh[0] - NA.x) + (xl[0] - NB.x);
-    const float d1 = mi1(xh[1] - NA.y) + (xl[1] - NB.y);
-    const float dz = mi1(xh[2] - NA.z) + (xl[2] - NB.z);
-    const float d2 = fmaf(d0, d0, fmaf(d1, d1, dz * dz));
-    int dec;
-    if (e2 >= A.rc2_lo) {
-      dec = DEC_UNSURE;
-    } else {
-      const float fx = ax + hs, fy = ay + hs, fz = az + hs;
-      const float far2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
-      const float lhs = s * s;
-      const float cmax = fmaxf(ax, fmaxf(ay, az));
-      const int a1 = lhs < A.th2_lo * d2 ? 1 : (lhs > A.th2_hi * d2 ? 0 : 2);
-      const int a2 = cmax > A.lim_hi * s ? 1 : (cmax < A.lim_lo * s ? 0 : 2);
-      const int a3 = far2 < A.rc2_lo ? 1 : (far2 > A.rc2_hi ? 0 : 2);
-      if (a1 == 0 || a2 == 0 || a3 == 0) dec = DEC_OPEN;
-      else if (a1 == 2 || a2 == 2 || a3 == 2) dec = DEC_UNSURE;
-      else dec = d2 < A.rc2_lo ? DEC_ACCEPT : (d2 > A.rc2_hi ? DEC_ACCEPT_OUT : DEC_UNSURE);
-    }
-    if (dec == DEC_UNSURE) dec = decide_exact(A, k, node, meta_level(ND.w));
-    return dec;
+  __device__ __forceinline__ int decide_for(const WalkArgs& A, const Smem& M, int t, int64_t kt, int node,
+                                            const int4& ND, const float4& NC, const float4& NA,
+                                            const float4& NB) const {
+    return decide_f32(A, kt, M.tA[t], M.tB[t], node, ND, NC, NA, NB);
   }
 
-  // Stage slot s of the queue into batch position `lane`; returns the lane
-  // mask of its queue entry.
-  __device__ __forceinline__ uint32_t stage(const WalkArgs& A, const WarpBufs& W, Smem& M, int nq, int s, int lane,
-                                            const GroupInfo& G, int64_t gbase, float Rg) {
+  __device__ __forceinline__ Fetch fetch(const WalkArgs& A, const WarpBufs& W, int nq, int s) const {
+    Fetch f;
     const int e = entry_of(W, nq, s);
     const int4 Q = W.queue[e];
-    float4 a, b;
-    int id;
-    float lo, hi;
-    const bool node = Q.y < 0;
-    if (node) {
-      a = A.T.nA[Q.x];
-      b = A.T.nB[Q.x];
-      id = -2 - Q.x;
-      lo = hi = __int_as_float(0x7f800000);  // accepted node: inside the cut by decision
+    f.node = Q.y < 0;
+    if (f.node) {
+      f.a = A.T.nA[Q.x];
+      f.b = A.T.nB[Q.x];
+      f.id = -2 - Q.x;
     } else {
       const int j = Q.x + (s - W.qoff[e]);
-      a = A.T.pA[j];
-      b = A.T.pB[j];
-      id = j;
-      lo = A.pp_lo;
-      hi = A.pp_hi;
+      f.a = A.T.pA[j];
+      f.b = A.T.pB[j];
+      f.id = j;
     }
-    const bool uni = (Q.w & 1) != 0;
+    f.flags = Q.w;
+    f.q = (uint32_t)Q.z;
+    return f;
+  }
+
+  // Stage a fetched source into batch position `lane` (or an empty slot).
+  // Filter form: (-2 x, -2 y, -2 z, |x|^2 - r_cut^2 - margin) relative to the
+  // group centre, so |x_i - x_j|^2 - r_cut^2 - margin evaluates as
+  // fW + |x_i|^2 + fX x_i + fY y_i + fZ z_i.  The FP32 evaluation of that
+  // chain is within 18 u (|x_i| + |x_j|)^2 + 18 u r_cut^2 of the exact value
+  // (u = 2^-24); the margin is 64 u times that bound's bracket, so every pair
+  // inside the cut gives a negative value.
+  __device__ __forceinline__ void stage(const WalkArgs& A, Stage& S, Smem& M, const Fetch& f, bool has, int lane,
+                                        const GroupInfo& G, int64_t gbase, float Rg) const {
+    float4 a = f.a;
+    const float4 b = f.b;
+    const bool uni = (f.flags & 1) != 0;
     if (uni) {
-      a.x -= shift_of(Q.w, 0);
-      a.y -= shift_of(Q.w, 1);
-      a.z -= shift_of(Q.w, 2);
+      a.x -= shift_of(f.flags, 0);
+      a.y -= shift_of(f.flags, 1);
+      a.z -= shift_of(f.flags, 2);
     }
-    float4 f = make_float4(0.f, 0.f, 0.f, -1e30f);  // always a candidate
-    if (uni && !node) {
-      // conservative margin: the FP32 evaluation of |x_i - x_j|^2 below is
-      // within 18 u (|x_i| + |x_j|)^2 of the exact value (u = 2^-24)
-      const float x0 = (a.x - G.cx) + b.x, x1 = (a.y - G.cy) + b.y, x2 = (a.z - G.cz) + b.z;
-      const float sj = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
-      const float rr = sqrtf(sj) + Rg;
-      f = make_float4(-2.f * x0, -2.f * x1, -2.f * x2, sj - 3.814697265625e-06f * rr * rr);
+    float fx = 0.f, fy = 0.f, fz = 0.f, fw = 1e30f;  // empty slot: never a candidate
+    if (has) {
+      fw = -1e30f;  // accepted node or per-pair image: always a candidate
+      if (uni && !f.node) {
+        const float x0 = (a.x - G.cx) + b.x, x1 = (a.y - G.cy) + b.y, x2 = (a.z - G.cz) + b.z;
+        const float sj = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
+        const float rr = sqrtf(sj) + Rg;
+        fx = -2.f * x0;
+        fy = -2.f * x1;
+        fz = -2.f * x2;
+        fw = (sj - A.rc2_hi) - 3.814697265625e-06f * fmaf(rr, rr, A.rc2_hi);
+      }
+      const float lo = f.node ? __int_as_float(0x7f800000) : A.pp_lo;  // accepted node: inside by decision
+      const float hi = f.node ? __int_as_float(0x7f800000) : A.pp_hi;
+      S.sa[lane] = a;
+      S.sb[lane] = b;
+      S.sc[lane] = make_int4(f.id, uni ? 0 : 1, __float_as_int(lo), __float_as_int(hi));
+      if (f.id >= gbase && f.id < gbase + kGroup) M.self[f.id - gbase] = lane;
     }
-    M.sa[lane] = a;
-    M.sb[lane] = b;
-    M.sf[lane] = f;
-    M.sc[lane] = make_int4(id, uni ? 0 : 1, __float_as_int(lo), __float_as_int(hi));
-    if (id >= gbase && id < gbase + kGroup) M.self[id - gbase] = lane;
-    return (uint32_t)Q.z;
+    S.fX[lane] = fx;
+    S.fY[lane] = fy;
+    S.fZ[lane] = fz;
+    S.fW[lane] = fw;
   }
 
   __device__ __forceinline__ void fold() {
@@ -454,10 +515,11 @@ struct LaneF32 {
   // Target i of the group against staged slot s: the exact cut decision, and
   // the interaction (target-side term, hit flag).  In the adjoint the
   // source-side terms are added to the slot's shared sums.
-  __device__ __forceinline__ float4 pair_eval(const WalkArgs& A, Smem& M, int i, int s, int64_t gbase) {
+  __device__ __forceinline__ float4 pair_eval(const WalkArgs& A, const Stage& St, Smem& M, int i, int s,
+                                              int64_t gbase) const {
     const float4 ta = M.tA[i], tb = M.tB[i];
-    const float4 a = M.sa[s], b = M.sb[s];
-    const int4 c = M.sc[s];
+    const float4 a = St.sa[s], b = St.sb[s];
+    const int4 c = St.sc[s];
     float dh0 = ta.x - a.x, dh1 = ta.y - a.y, dh2 = ta.z - a.z;
     if (c.y) {
       dh0 = mi1(dh0);
@@ -493,35 +555,56 @@ struct LaneF32 {
   }
 
   // Evaluate the queued entries (see the header comment).
-  __device__ void evaluate(const WalkArgs& A, const WarpBufs& W, Smem& M, int nq, int lane, const GroupInfo& G,
-                           int64_t gbase, uint32_t vmask, float Rg) {
+  __device__ void evaluate(const WalkArgs& A, const WarpBufs& W, Stage& St, Smem& M, int nq, int lane,
+                           const GroupInfo& G, int64_t gbase, uint32_t vmask, float Rg) {
     const int total = queue_offsets(A, W, nq, lane);
     if (total < 0) {
       if (lane == 0) set_status(A.wsb, ST_TREELINK);
       return;
     }
+    const unsigned long long X2 = pack2(xr[0], xr[0]), Y2 = pack2(xr[1], xr[1]), Z2 = pack2(xr[2], xr[2]);
+    const unsigned long long S2 = pack2(sr, sr);
+    Fetch nx = {};
+    if (lane < total) nx = fetch(A, W, nq, lane);
     for (int base = 0; base < total; base += kSlots) {
       const int cnt = min(kSlots, total - base);
       M.self[lane] = -1;
       if (ADJ) M.sG[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       __syncwarp();
-      uint32_t q = 0;
-      if (lane < cnt) q = stage(A, W, M, nq, base + lane, lane, G, gbase, Rg);
+      const bool has = lane < cnt;
+      stage(A, St, M, nx, has, lane, G, gbase, Rg);
+      const uint32_t q = has ? nx.q : 0u;
+      // fetch the next batch while this one is evaluated
+      if (base + kSlots + lane < total) nx = fetch(A, W, nq, base + kSlots + lane);
       __syncwarp();
       // bit s of msk: slot s is in this lane's part of its entry's lane mask
       const uint32_t cm = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
       uint32_t msk;
-      if (__any_sync(0xffffffffu, lane < cnt && q != vmask)) msk = transpose32(q, lane);
+      if (__any_sync(0xffffffffu, has && q != vmask)) msk = transpose32(q, lane);
       else msk = valid ? cm : 0u;
-      // conservative cut test for every staged slot
-      uint32_t hit = 0;
-#pragma unroll 8
-      for (int s = 0; s < cnt; ++s) {
-        const float4 f = M.sf[s];
-        const float r2 = fmaf(f.x, xr[0], fmaf(f.y, xr[1], fmaf(f.z, xr[2], f.w + sr)));
-        hit |= (r2 < A.rc2_hi ? 1u : 0u) << s;
+      // conservative cut test for all 32 slots, two per instruction; the sign
+      // bit of each result is shifted into acc (slot 0 ends up at bit 31)
+      uint32_t acc = 0;
+#pragma unroll
+      for (int s = 0; s < kSlots; s += 4) {
+        const float4 fx = *reinterpret_cast<const float4*>(St.fX + s);
+        const float4 fy = *reinterpret_cast<const float4*>(St.fY + s);
+        const float4 fz = *reinterpret_cast<const float4*>(St.fZ + s);
+        const float4 fw = *reinterpret_cast<const float4*>(St.fW + s);
+        unsigned long long r01 = add2(pack2(fw.x, fw.y), S2);
+        unsigned long long r23 = add2(pack2(fw.z, fw.w), S2);
+        r01 = fma2(pack2(fz.x, fz.y), Z2, r01);
+        r23 = fma2(pack2(fz.z, fz.w), Z2, r23);
+        r01 = fma2(pack2(fy.x, fy.y), Y2, r01);
+        r23 = fma2(pack2(fy.z, fy.w), Y2, r23);
+        r01 = fma2(pack2(fx.x, fx.y), X2, r01);
+        r23 = fma2(pack2(fx.z, fx.w), X2, r23);
+        acc = __funnelshift_l((uint32_t)r01, acc, 1);
+        acc = __funnelshift_l((uint32_t)(r01 >> 32), acc, 1);
+        acc = __funnelshift_l((uint32_t)r23, acc, 1);
+        acc = __funnelshift_l((uint32_t)(r23 >> 32), acc, 1);
       }
-      hit &= msk;
+      uint32_t hit = __brev(acc) & msk;
       const int so = M.self[lane];
       if (so >= 0) hit &= ~(1u << so);
       // compaction: target-major pair list
@@ -540,21 +623,22 @@ struct LaneF32 {
         while (m) {
           const int s = __ffs(m) - 1;
           m &= m - 1;
-          M.list[t++] = (unsigned short)((lane << 5) | s);
+          W.list[t++] = (unsigned short)((lane << 5) | s);
         }
       }
       __syncwarp();
       for (int wb = 0; wb < T; wb += kWin) {
         const int we = min(T, wb + kWin);
         for (int p = wb + lane; p < we; p += 32) {
-          const int e = M.list[p];
-          M.F[p - wb] = pair_eval(A, M, e >> 5, e & 31, gbase);
+          const int e = W.list[p];
+          St.F[p - wb] = pair_eval(A, St, M, e >> 5, e & 31, gbase);
         }
         __syncwarp();
         // each target sums its own results in slot order
         const int lo = max(off, wb), hi = min(off + c, we);
+#pragma unroll 4
         for (int t = lo; t < hi; ++t) {
-          const float4 v = M.F[t - wb];
+          const float4 v = St.F[t - wb];
           P[0] += v.x;
           P[1] += v.y;
           P[2] += v.z;
@@ -563,10 +647,10 @@ struct LaneF32 {
         __syncwarp();
       }
       fold();
-      if (ADJ && lane < cnt) {
+      if (ADJ && has) {
         const float4 g = M.sG[lane];
         if (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f) {
-          const int id = M.sc[lane].x;
+          const int id = St.sc[lane].x;
           double* Gd = id >= 0 ? A.Gp + 3 * (int64_t)id : A.Gn + 3 * (int64_t)(-2 - id);
           double* Sd = id >= 0 ? A.Sp + id : A.Sn + (-2 - id);
           atomicAdd(Gd, f2d_exact(g.x));
@@ -598,6 +682,9 @@ struct LaneF32 {
 // evaluates every staged slot in lockstep.
 struct LaneF64 {
   struct Smem {
+    int unused;
+  };
+  struct Stage {
     double slot[kSlots * 6];  // per slot: double x, y, z, m, h; int id, int lane mask
   };
 
@@ -621,14 +708,16 @@ struct LaneF64 {
     nint = 0;
   }
 
-  __device__ int decide(const WalkArgs& A, int node, const int4& ND, const float4&, const float4&, const float4&) {
-    return decide_exact(A, k, node, meta_level(ND.w));
+  __device__ __forceinline__ int decide_for(const WalkArgs& A, const Smem&, int, int64_t kt, int node,
+                                            const int4& ND, const float4&, const float4&, const float4&) const {
+    return decide_exact(A, kt, node, meta_level(ND.w));
   }
 
-  __device__ __forceinline__ void stage(const WalkArgs& A, const WarpBufs& W, Smem& M, int nq, int s, int lane) {
+  __device__ __forceinline__ void stage(const WalkArgs& A, const WarpBufs& W, Stage& S, int nq, int s,
+                                        int lane) const {
     const int e = entry_of(W, nq, s);
     const int4 Q = W.queue[e];
-    double* d = M.slot + 6 * lane;
+    double* d = S.slot + 6 * lane;
     int* ii = reinterpret_cast<int*>(d + 5);
     if (Q.y < 0) {
       const int n = Q.x;
@@ -650,8 +739,8 @@ struct LaneF64 {
     ii[1] = Q.z;
   }
 
-  __device__ __forceinline__ void pair(const WalkArgs& A, const Smem& M, int t, int lane) {
-    const double* d = M.slot + 6 * t;
+  __device__ __forceinline__ void pair(const WalkArgs& A, const Stage& S, int t, int lane) {
+    const double* d = S.slot + 6 * t;
     const int* ii = reinterpret_cast<const int*>(d + 5);
     const int id = ii[0];
     const bool mine = valid && ((ii[1] >> lane) & 1) && id != k;
@@ -680,8 +769,8 @@ struct LaneF64 {
     ++nint;
   }
 
-  __device__ void evaluate(const WalkArgs& A, const WarpBufs& W, Smem& M, int nq, int lane, const GroupInfo&,
-                           int64_t, uint32_t, float) {
+  __device__ void evaluate(const WalkArgs& A, const WarpBufs& W, Stage& St, Smem&, int nq, int lane,
+                           const GroupInfo&, int64_t, uint32_t, float) {
     const int total = queue_offsets(A, W, nq, lane);
     if (total < 0) {
       if (lane == 0) set_status(A.wsb, ST_TREELINK);
@@ -689,9 +778,9 @@ struct LaneF64 {
     }
     for (int base = 0; base < total; base += kSlots) {
       const int cnt = min(kSlots, total - base);
-      if (lane < cnt) stage(A, W, M, nq, base + lane, lane);
+      if (lane < cnt) stage(A, W, St, nq, base + lane, lane);
       __syncwarp();
-      for (int t = 0; t < cnt; ++t) pair(A, M, t, lane);
+      for (int t = 0; t < cnt; ++t) pair(A, St, t, lane);
       __syncwarp();
     }
   }
@@ -708,10 +797,18 @@ struct LaneF64 {
 // ------------------------------------------------------------------ traversal
 
 template <class Lane>
+union WarpScratch {
+  MixedScratch mix;
+  typename Lane::Stage stage;
+};
+
+template <class Lane>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   __shared__ int2 s_stack[kWarpsPerBlock][kStack];
   __shared__ int4 s_queue[kWarpsPerBlock][kQueue];
   __shared__ int s_qoff[kWarpsPerBlock][kQueue + 1];
+  __shared__ unsigned short s_list[kWarpsPerBlock][kList];
+  __shared__ WarpScratch<Lane> s_scr[kWarpsPerBlock];
   __shared__ typename Lane::Smem s_lane[kWarpsPerBlock];
   const TreeDev& T = A.T;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -725,6 +822,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   W.stack = s_stack[wib];
   W.queue = s_queue[wib];
   W.qoff = s_qoff[wib];
+  W.list = s_list[wib];
+  MixedScratch& X = s_scr[wib].mix;
+  typename Lane::Stage& St = s_scr[wib].stage;
   typename Lane::Smem& M = s_lane[wib];
   int nodes_total = 0;
   for (int l = 0; l < kLevels; ++l) nodes_total += T.sb->level_cnt[l];
@@ -760,10 +860,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
         if (lane == 0) set_status(A.wsb, ST_STACK);
         break;
       }
-      // Pop whole child ranges from the top until up to 32 nodes are gathered.
-      // The index is clamped so no lane forms an address outside the stack,
-      // and every pop completes before any push.
-      const int m = min(sp, 32);
+      // Pop whole child ranges from the top until up to 32 nodes are gathered
+      // (one range when the stack is deep).  The index is clamped so no lane
+      // forms an address outside the stack, and every pop completes before
+      // any push.
+      const int m = sp > kDeep ? 1 : min(sp, 32);
       const int2 E = W.stack[max(sp - 1 - lane, 0)];
       __syncwarp();
       const uint32_t ex = (uint32_t)E.x;
@@ -838,55 +939,63 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
             cls == CL_ACCEPT ? make_int4(node, -1, (int)mask, fl) : make_int4(ND.x, ND.y, (int)mask, fl);
       }
       nq += __popc(qm);
-      // MIXED nodes: exact per-lane decisions, one node at a time; the node's
-      // data comes from the lane that loaded it
-      uint32_t mm = __ballot_sync(0xffffffffu, cls == CL_MIXED);
-      while (mm) {
-        const int src = __ffs(mm) - 1;
-        mm &= mm - 1;
-        const int mnode = __shfl_sync(0xffffffffu, node, src);
-        const uint32_t mmask = (uint32_t)__shfl_sync(0xffffffffu, (int)mask, src);
-        int4 MD;
-        MD.x = __shfl_sync(0xffffffffu, ND.x, src);
-        MD.y = __shfl_sync(0xffffffffu, ND.y, src);
-        MD.z = __shfl_sync(0xffffffffu, ND.z, src);
-        MD.w = __shfl_sync(0xffffffffu, ND.w, src);
-        float4 MC, MA, MB;
-        MC.x = __shfl_sync(0xffffffffu, NC.x, src);
-        MC.y = __shfl_sync(0xffffffffu, NC.y, src);
-        MC.z = __shfl_sync(0xffffffffu, NC.z, src);
-        MC.w = __shfl_sync(0xffffffffu, NC.w, src);
-        MA.x = __shfl_sync(0xffffffffu, NA.x, src);
-        MA.y = __shfl_sync(0xffffffffu, NA.y, src);
-        MA.z = __shfl_sync(0xffffffffu, NA.z, src);
-        MA.w = __shfl_sync(0xffffffffu, NA.w, src);
-        MB.x = __shfl_sync(0xffffffffu, NB.x, src);
-        MB.y = __shfl_sync(0xffffffffu, NB.y, src);
-        MB.z = __shfl_sync(0xffffffffu, NB.z, src);
-        MB.w = __shfl_sync(0xffffffffu, NB.w, src);
-        const bool act = valid && ((mmask >> lane) & 1u);
-        const int dec = act ? L.decide(A, mnode, MD, MC, MA, MB) : DEC_DISCARD;
-        const uint32_t am = __ballot_sync(0xffffffffu, dec == DEC_ACCEPT);
-        const uint32_t om = __ballot_sync(0xffffffffu, dec == DEC_OPEN);
-        const int fl = image_flags(A, G, MC);
-        if (am) {
-          if (lane == 0) W.queue[nq] = make_int4(mnode, -1, (int)am, fl);
-          ++nq;
+      // MIXED nodes: exact decisions for every (node, target in its mask),
+      // 32 at a time from a node-major list; the results are OR-ed into
+      // per-node accept / open masks
+      const uint32_t mm = __ballot_sync(0xffffffffu, cls == CL_MIXED);
+      if (mm) {
+        const int nm = __popc(mm);
+        if (cls == CL_MIXED) {
+          const int ix = __popc(mm & lt);
+          X.node[ix] = node;
+          X.D[ix] = ND;
+          X.C[ix] = NC;
+          X.A[ix] = NA;
+          X.B[ix] = NB;
+          X.mask[ix] = mask & vmask;
+          X.acc[ix] = 0u;
+          X.open[ix] = 0u;
         }
-        if (om) {
-          if (meta_leaf(MD.w)) {
-            if (lane == 0) W.queue[nq] = make_int4(MD.x, MD.y, (int)om, fl);
-            ++nq;
-          } else {
-            const uint32_t mch = (uint32_t)meta_nchild(MD.w);
-            if (lane == 0) W.stack[sp] = make_int2((int)((uint32_t)MD.z | (mch << 28)), (int)om);
-            ++sp;
-          }
+        __syncwarp();
+        int nd = 0;
+        for (int ix = 0; ix < nm; ++ix) {
+          const uint32_t mk = X.mask[ix];
+          if ((mk >> lane) & 1u) W.list[nd + __popc(mk & lt)] = (unsigned short)((ix << 5) | lane);
+          nd += __popc(mk);
         }
+        __syncwarp();
+        for (int d = lane; d < nd; d += 32) {
+          const int e = W.list[d];
+          const int ix = e >> 5, t = e & 31;
+          const int dec = L.decide_for(A, M, t, gbase + t, X.node[ix], X.D[ix], X.C[ix], X.A[ix], X.B[ix]);
+          if (dec == DEC_ACCEPT) atomicOr(&X.acc[ix], 1u << t);
+          else if (dec == DEC_OPEN) atomicOr(&X.open[ix], 1u << t);
+        }
+        __syncwarp();
+        const bool hm = lane < nm;
+        const int hx = hm ? lane : 0;
+        const uint32_t am = hm ? X.acc[hx] : 0u;
+        const uint32_t om = hm ? X.open[hx] : 0u;
+        const int4 XD = X.D[hx];
+        const int xnode = X.node[hx];
+        const bool xleaf = meta_leaf(XD.w);
+        const int fl = (am | om) ? image_flags(A, G, X.C[hx]) : 0;
+        const bool qa = am != 0u, qo = om != 0u && xleaf, po = om != 0u && !xleaf;
+        const uint32_t ba = __ballot_sync(0xffffffffu, qa);
+        const uint32_t bo = __ballot_sync(0xffffffffu, qo);
+        const uint32_t bp = __ballot_sync(0xffffffffu, po);
+        if (qa) W.queue[nq + __popc(ba & lt)] = make_int4(xnode, -1, (int)am, fl);
+        nq += __popc(ba);
+        if (qo) W.queue[nq + __popc(bo & lt)] = make_int4(XD.x, XD.y, (int)om, fl);
+        nq += __popc(bo);
+        if (po)
+          W.stack[sp + __popc(bp & lt)] =
+              make_int2((int)((uint32_t)XD.z | ((uint32_t)meta_nchild(XD.w) << 28)), (int)om);
+        sp += __popc(bp);
       }
       __syncwarp();
     } else if (nq > 0) {
-      L.evaluate(A, W, M, nq, lane, G, gbase, vmask, Rg);
+      L.evaluate(A, W, St, M, nq, lane, G, gbase, vmask, Rg);
       nq = 0;
       __syncwarp();
     } else {
