@@ -65,15 +65,15 @@ __device__ __forceinline__ uint64_t hilbert63(uint32_t a, uint32_t b, uint32_t c
   return (spread3(a) << 2) | (spread3(b) << 1) | spread3(c);
 }
 
-__global__ void k_keys(const double* __restrict__ pos, int64_t n, double L, uint64_t* __restrict__ keys,
+__global__ void k_keys(const double* __restrict__ pos, int64_t n, BoxScale B, uint64_t* __restrict__ keys,
                        int32_t* __restrict__ vals, StatusBlock* sb) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double x0 = pos[3 * i], x1 = pos[3 * i + 1], x2 = pos[3 * i + 2];
     uint64_t key = 0;
     if (isfinite(x0) && isfinite(x1) && isfinite(x2)) {
-      const uint32_t q0 = quantise(wrap_coord(x0, L), L);
-      const uint32_t q1 = quantise(wrap_coord(x1, L), L);
-      const uint32_t q2 = quantise(wrap_coord(x2, L), L);
+      const uint32_t q0 = quantise(wrap_coord(x0, B), B);
+      const uint32_t q1 = quantise(wrap_coord(x1, B), B);
+      const uint32_t q2 = quantise(wrap_coord(x2, B), B);
       key = hilbert63(q0, q1, q2);
     } else {
       set_status(sb, ST_BADINPUT);
@@ -241,7 +241,7 @@ cudaError_t launch_keys_sort(const double* pos, int64_t n, double L, uint64_t* k
   const int kb = 256;
   int64_t kgrid = (n + kb - 1) / kb;
   if (kgrid > 152 * 64) kgrid = 152 * 64;
-  k_keys<<<(unsigned)kgrid, kb, 0, s>>>(pos, n, L, keys_out, order_out, W.sb);
+  k_keys<<<(unsigned)kgrid, kb, 0, s>>>(pos, n, box_scale(L), keys_out, order_out, W.sb);
   uint64_t* kin = keys_out;
   int32_t* vin = order_out;
   uint64_t* ko = W.keys_alt;

@@ -2,6 +2,7 @@
 // of libog.so (not part of the public ABI; see include/og.h).
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -202,22 +203,39 @@ __device__ inline void split_coord(double xi, float& hi, float& lo) {
   lo = static_cast<float>(xi - h);
 }
 
+// Division by the box side.  When L is a power of two, x / L equals
+// x * (1 / L) exactly (both are the correctly rounded value of x 2^-e), so the
+// multiply is used; any other L takes the IEEE division.
+struct BoxScale {
+  double L, invL;
+  int pow2;
+};
+
+inline BoxScale box_scale(double L) {
+  int e = 0;
+  const double m = std::frexp(L, &e);
+  return BoxScale{L, 1.0 / L, m == 0.5 ? 1 : 0};
+}
+
+__device__ inline double div_box(double x, const BoxScale& B) {
+  return B.pow2 ? __dmul_rn(x, B.invL) : __ddiv_rn(x, B.L);
+}
+
 // Periodic wrap into [0, L]: x - L floor(x / L), each operation rounded once
 // (no fused multiply-add: the result must be bit-identical to the host form).
-__device__ inline double wrap_coord(double x, double L) {
-  double fl = floor(__ddiv_rn(x, L));
-  double prod = __dmul_rn(L, fl);
+__device__ inline double wrap_coord(double x, const BoxScale& B) {
+  double fl = floor(div_box(x, B));
+  double prod = __dmul_rn(B.L, fl);
   return __dsub_rn(x, prod);
 }
 
-__device__ inline uint32_t quantise(double w, double L) {
-  double t = __dmul_rn(__ddiv_rn(w, L), 2097152.0);
+__device__ inline uint32_t quantise(double w, const BoxScale& B) {
+  double t = __dmul_rn(div_box(w, B), 2097152.0);
   double fl = floor(t);
   if (fl < 0.0) return 0u;
   if (fl > 2097151.0) return 2097151u;
   return static_cast<uint32_t>(fl);
 }
-
 
 // Arguments of the tree build launches.
 struct BuildArgs {

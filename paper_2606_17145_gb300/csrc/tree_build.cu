@@ -19,18 +19,17 @@
 namespace og {
 
 
-__global__ void k_permute(BuildArgs A) {
+__global__ void k_permute(BuildArgs A, BoxScale B) {
   const TreeDev& T = A.T;
-  const double L = A.L;
-  const double invL2 = 1.0 / (L * L);
+  const double invL2 = B.invL * B.invL;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < T.n; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t i = A.order[k];
     double w[3];
     float hi[3], lo[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      w[c] = wrap_coord(A.pos[3 * (int64_t)i + c], L);
-      split_coord(w[c] / L, hi[c], lo[c]);
+      w[c] = wrap_coord(A.pos[3 * (int64_t)i + c], B);
+      split_coord(div_box(w[c], B), hi[c], lo[c]);
       T.x64[3 * k + c] = w[c];
     }
     const double m = A.mass[i];
@@ -39,7 +38,7 @@ __global__ void k_permute(BuildArgs A) {
           isfinite(A.pos[3 * (int64_t)i + 2]) && m > 0.0 && isfinite(m) && eps > 0.0 && isfinite(eps)))
       set_status(T.sb, ST_BADINPUT);
     const double h = 2.8 * eps;
-    const double hb = h / L;
+    const double hb = h * B.invL;
     T.m64[k] = m;
     T.h64[k] = h;
     T.order[k] = i;
@@ -48,14 +47,14 @@ __global__ void k_permute(BuildArgs A) {
   }
 }
 
-__global__ void k_groups(TreeDev T, double L) {
+__global__ void k_groups(TreeDev T, BoxScale B) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < T.ngroups; g += (int64_t)gridDim.x * blockDim.x) {
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     const int64_t a = g * kGroup, b = (T.n < a + kGroup ? T.n : a + kGroup);
     for (int64_t k = a; k < b; ++k)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double x = T.x64[3 * k + c] / L;
+        const double x = div_box(T.x64[3 * k + c], B);
         lo[c] = fmin(lo[c], x);
         hi[c] = fmax(hi[c], x);
       }
@@ -157,14 +156,14 @@ __global__ void __launch_bounds__(256) k_expand(TreeDev T, const uint64_t* __res
 }
 
 // Bottom-up moments for one level.  8 lanes per node.
-__global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, double L) {
+__global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, BoxScale B) {
   const int base = level_base(T.sb, lev);
   const int cnt = T.sb->level_cnt[lev];
   if (base + cnt > T.cap) return;  // capacity already exceeded (flagged by k_expand)
   const int sub = threadIdx.x & 7;
-  const double side = ldexp(L, -lev);
+  const double side = ldexp(B.L, -lev);
   const float side_b = ldexpf(1.0f, -lev);
-  const double invL = 1.0 / L, invL2 = 1.0 / (L * L);
+  const double invL = B.invL, invL2 = B.invL * B.invL;
   // warp-uniform loop bound: the 4 node groups of a warp stay together for the shuffles
   const int stride = (gridDim.x * blockDim.x) >> 3;
   for (int wstep = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3; wstep < cnt; wstep += stride) {
@@ -201,14 +200,15 @@ __global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, double L) {
       H = fmax(H, __shfl_xor_sync(0xffffffffu, H, o, 8));
     }
     if (live && sub == 0) {
-      const double com[3] = {S0 / M, S1 / M, S2 / M};
+      const double invM = 1.0 / M;
+      const double com[3] = {S0 * invM, S1 * invM, S2 * invM};
       float hi[3], lo[3];
       double cen[3];
       float cenb[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         split_coord(com[c] * invL, hi[c], lo[c]);
-        const uint32_t q = quantise(T.x64[3 * (int64_t)D.x + c], L) >> (kMaxLevel - lev);
+        const uint32_t q = quantise(T.x64[3 * (int64_t)D.x + c], B) >> (kMaxLevel - lev);
         cen[c] = __dmul_rn((double)q + 0.5, side);
         cenb[c] = ((float)q + 0.5f) * side_b;
       }
@@ -234,16 +234,17 @@ cudaError_t launch_tree_build(const BuildArgs& A, cudaStream_t s) {
   const TreeDev& T = A.T;
   int64_t grid = (T.n + 255) / 256;
   if (grid > 152 * 32) grid = 152 * 32;
-  k_permute<<<(unsigned)grid, 256, 0, s>>>(A);
+  const BoxScale B = box_scale(A.L);
+  k_permute<<<(unsigned)grid, 256, 0, s>>>(A, B);
   int64_t ggrid = (T.ngroups + 127) / 128;
   if (ggrid > 152 * 16) ggrid = 152 * 16;
-  k_groups<<<(unsigned)ggrid, 128, 0, s>>>(T, A.L);
+  k_groups<<<(unsigned)ggrid, 128, 0, s>>>(T, B);
   k_root<<<1, 32, 0, s>>>(T, A.leaf_size);
   // Grids are fixed (the per-level node count lives on the device); blocks
   // stride over the level.
   const unsigned egrid = 152 * 8;
   for (int lev = 0; lev < kMaxLevel; ++lev) k_expand<<<egrid, 256, 0, s>>>(T, A.keys, lev, A.leaf_size);
-  for (int lev = kMaxLevel; lev >= 0; --lev) k_moments<<<egrid, 256, 0, s>>>(T, lev, A.L);
+  for (int lev = kMaxLevel; lev >= 0; --lev) k_moments<<<egrid, 256, 0, s>>>(T, lev, B);
   return cudaGetLastError();
 }
 

@@ -384,7 +384,8 @@ struct LaneF32 {
     float4 tA[kGroup];    // targets: hi part, h^2
     float4 tB[kGroup];    // targets: lo part
     float4 tW[ADJ ? kGroup : 1];   // adjoint: dL/da of each target
-    float4 sG[ADJ ? kSlots : 1];   // adjoint: source-side sums of the batch (G, S) per slot
+    uint32_t hitw[ADJ ? kGroup : 1];   // adjoint: each target's hit mask of the batch
+    int offw[ADJ ? kGroup : 1];        // adjoint: each target's first position in the pair list
     int self[kGroup];     // staged slot holding the target itself, or -1
   };
   // per-batch staging (dead between evaluations; shares memory with the
@@ -395,6 +396,7 @@ struct LaneF32 {
     int4 sc[kSlots];      // id (particle, or -2 - node), per-pair image flag, cut band lo / hi (float bits)
     float fX[kSlots], fY[kSlots], fZ[kSlots], fW[kSlots];  // filter form (see stage)
     float4 F[kWin];       // pair results of the current window (target side, hit flag)
+    float4 SG[ADJ ? kWin : 1];  // adjoint: source-side terms of the window's pairs (G, S)
   };
   // a slot's source, fetched one batch ahead
   struct Fetch {
@@ -514,9 +516,9 @@ struct LaneF32 {
 
   // Target i of the group against staged slot s: the exact cut decision, and
   // the interaction (target-side term, hit flag).  In the adjoint the
-  // source-side terms are added to the slot's shared sums.
-  __device__ __forceinline__ float4 pair_eval(const WalkArgs& A, const Stage& St, Smem& M, int i, int s,
-                                              int64_t gbase) const {
+  // source-side terms go to sg.
+  __device__ __forceinline__ float4 pair_eval(const WalkArgs& A, const Stage& St, const Smem& M, int i, int s,
+                                              int64_t gbase, float4& sg) const {
     const float4 ta = M.tA[i], tb = M.tB[i];
     const float4 a = St.sa[s], b = St.sb[s];
     const int4 c = St.sc[s];
@@ -533,6 +535,7 @@ struct LaneF32 {
     const float r2 = fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2]));
     bool in = r2 < __int_as_float(c.z);
     if (!in) in = c.x >= 0 && r2 <= __int_as_float(c.w) && pair_inside_exact(A, gbase + i, c.x);
+    sg = make_float4(0.f, 0.f, 0.f, 0.f);
     if (!in) return make_float4(0.f, 0.f, 0.f, 0.f);
     float F, Fr;
     force_f32<ADJ>(A, r2, fmaxf(ta.w, b.w), F, Fr);
@@ -546,10 +549,7 @@ struct LaneF32 {
       const float j0 = -fmaf(F, w.x, qq * dv[0]);
       const float j1 = -fmaf(F, w.y, qq * dv[1]);
       const float j2 = -fmaf(F, w.z, qq * dv[2]);
-      atomicAdd(&M.sG[s].x, j0);
-      atomicAdd(&M.sG[s].y, j1);
-      atomicAdd(&M.sG[s].z, j2);
-      atomicAdd(&M.sG[s].w, -F * dw);
+      sg = make_float4(j0, j1, j2, -F * dw);
       return make_float4(a.w * j0, a.w * j1, a.w * j2, 1.f);
     }
   }
@@ -569,7 +569,6 @@ struct LaneF32 {
     for (int base = 0; base < total; base += kSlots) {
       const int cnt = min(kSlots, total - base);
       M.self[lane] = -1;
-      if (ADJ) M.sG[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       __syncwarp();
       const bool has = lane < cnt;
       stage(A, St, M, nx, has, lane, G, gbase, Rg);
@@ -617,6 +616,16 @@ struct LaneF32 {
       }
       const int T = __shfl_sync(0xffffffffu, incl, 31);
       const int off = incl - c;
+      // adjoint: lane s owns slot s; its pairs are the targets of column s of
+      // the hit matrix, at list positions off_i + popc(hit_i below s), which
+      // increase with i
+      uint32_t col = 0u;
+      float gs[4] = {0.f, 0.f, 0.f, 0.f};
+      if (ADJ) {
+        M.hitw[lane] = hit;
+        M.offw[lane] = off;
+        col = transpose32(hit, lane);
+      }
       {
         uint32_t m = hit;
         int t = off;
@@ -631,7 +640,9 @@ struct LaneF32 {
         const int we = min(T, wb + kWin);
         for (int p = wb + lane; p < we; p += 32) {
           const int e = W.list[p];
-          St.F[p - wb] = pair_eval(A, St, M, e >> 5, e & 31, gbase);
+          float4 sg;
+          St.F[p - wb] = pair_eval(A, St, M, e >> 5, e & 31, gbase, sg);
+          if (ADJ) St.SG[p - wb] = sg;
         }
         __syncwarp();
         // each target sums its own results in slot order
@@ -644,20 +655,32 @@ struct LaneF32 {
           P[2] += v.z;
           nint += (int)v.w;
         }
+        if (ADJ) {
+          // source-side sums of slot `lane`, in target order
+          const uint32_t below = (1u << lane) - 1u;
+          while (col) {
+            const int i = __ffs(col) - 1;
+            const int pos = M.offw[i] + __popc(M.hitw[i] & below);
+            if (pos >= we) break;
+            const float4 v = St.SG[pos - wb];
+            gs[0] += v.x;
+            gs[1] += v.y;
+            gs[2] += v.z;
+            gs[3] += v.w;
+            col &= col - 1u;
+          }
+        }
         __syncwarp();
       }
       fold();
-      if (ADJ && has) {
-        const float4 g = M.sG[lane];
-        if (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f) {
-          const int id = St.sc[lane].x;
-          double* Gd = id >= 0 ? A.Gp + 3 * (int64_t)id : A.Gn + 3 * (int64_t)(-2 - id);
-          double* Sd = id >= 0 ? A.Sp + id : A.Sn + (-2 - id);
-          atomicAdd(Gd, f2d_exact(g.x));
-          atomicAdd(Gd + 1, f2d_exact(g.y));
-          atomicAdd(Gd + 2, f2d_exact(g.z));
-          atomicAdd(Sd, f2d_exact(g.w));
-        }
+      if (ADJ && has && (gs[0] != 0.f || gs[1] != 0.f || gs[2] != 0.f || gs[3] != 0.f)) {
+        const int id = St.sc[lane].x;
+        double* Gd = id >= 0 ? A.Gp + 3 * (int64_t)id : A.Gn + 3 * (int64_t)(-2 - id);
+        double* Sd = id >= 0 ? A.Sp + id : A.Sn + (-2 - id);
+        atomicAdd(Gd, f2d_exact(gs[0]));
+        atomicAdd(Gd + 1, f2d_exact(gs[1]));
+        atomicAdd(Gd + 2, f2d_exact(gs[2]));
+        atomicAdd(Sd, f2d_exact(gs[3]));
       }
       __syncwarp();
     }
