@@ -183,15 +183,15 @@ struct GroupInfo {
 // nodes and pushes at most one range per popped node (net growth <= 31).
 // Above kDeep entries a step pops a single range (<= 8 nodes, growth <= 7
 // per level), so the depth stays below kDeep + 31 + 7 x 20 + 8 for any tree.
-constexpr int kStack = 320;
+constexpr int kStack = 276;
 constexpr int kStackNeed = 32;   // pushes of one step
-constexpr int kDeep = 96;
+constexpr int kDeep = 64;
 static_assert(kDeep + 31 + 7 * 20 + 8 <= kStack - kStackNeed, "stack bound");
 constexpr int kQueue = 128;      // queued leaves / accepted nodes per warp
 constexpr int kQueueNeed = 64;   // a step queues at most 2 entries per node
 constexpr int kSlots = 32;       // sources staged per evaluation batch
 constexpr int kWin = 64;         // pair results held at once (FP32 evaluation)
-constexpr int kList = kSlots * kGroup;  // (node or slot, target) list entries
+constexpr int kList = 512;       // (node or slot, target) list entries
 
 // Stack entry: (first node | node count << 28, lane mask); node indices stay
 // below 2^28 (checked on the host).  Queue entry: (first particle or node,
@@ -393,7 +393,7 @@ struct LaneF32 {
   struct Stage {
     float4 sa[kSlots];    // staged source: hi part (image-shifted), mass
     float4 sb[kSlots];    // lo part, h^2
-    int4 sc[kSlots];      // id (particle, or -2 - node), per-pair image flag, cut band lo / hi (float bits)
+    int2 sc[kSlots];      // id (particle, or -2 - node), per-pair image flag
     float fX[kSlots], fY[kSlots], fZ[kSlots], fW[kSlots];  // filter form (see stage)
     float4 F[kWin];       // pair results of the current window (target side, hit flag)
     float4 SG[ADJ ? kWin : 1];  // adjoint: source-side terms of the window's pairs (G, S)
@@ -493,11 +493,9 @@ struct LaneF32 {
         fz = -2.f * x2;
         fw = (sj - A.rc2_hi) - 3.814697265625e-06f * fmaf(rr, rr, A.rc2_hi);
       }
-      const float lo = f.node ? __int_as_float(0x7f800000) : A.pp_lo;  // accepted node: inside by decision
-      const float hi = f.node ? __int_as_float(0x7f800000) : A.pp_hi;
       S.sa[lane] = a;
       S.sb[lane] = b;
-      S.sc[lane] = make_int4(f.id, uni ? 0 : 1, __float_as_int(lo), __float_as_int(hi));
+      S.sc[lane] = make_int2(f.id, uni ? 0 : 1);
       if (f.id >= gbase && f.id < gbase + kGroup) M.self[f.id - gbase] = lane;
     }
     S.fX[lane] = fx;
@@ -521,7 +519,7 @@ struct LaneF32 {
                                               int64_t gbase, float4& sg) const {
     const float4 ta = M.tA[i], tb = M.tB[i];
     const float4 a = St.sa[s], b = St.sb[s];
-    const int4 c = St.sc[s];
+    const int2 c = St.sc[s];
     float dh0 = ta.x - a.x, dh1 = ta.y - a.y, dh2 = ta.z - a.z;
     if (c.y) {
       dh0 = mi1(dh0);
@@ -533,8 +531,9 @@ struct LaneF32 {
     dv[1] = dh1 + (tb.y - b.y);
     dv[2] = dh2 + (tb.z - b.z);
     const float r2 = fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2]));
-    bool in = r2 < __int_as_float(c.z);
-    if (!in) in = c.x >= 0 && r2 <= __int_as_float(c.w) && pair_inside_exact(A, gbase + i, c.x);
+    // accepted node (id < 0): inside by decision; particle: cut band, then FP64
+    bool in = c.x < 0 || r2 < A.pp_lo;
+    if (!in) in = r2 <= A.pp_hi && pair_inside_exact(A, gbase + i, c.x);
     sg = make_float4(0.f, 0.f, 0.f, 0.f);
     if (!in) return make_float4(0.f, 0.f, 0.f, 0.f);
     float F, Fr;
@@ -606,71 +605,77 @@ struct LaneF32 {
       uint32_t hit = __brev(acc) & msk;
       const int so = M.self[lane];
       if (so >= 0) hit &= ~(1u << so);
-      // compaction: target-major pair list
-      const int c = __popc(hit);
-      int incl = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int T = __shfl_sync(0xffffffffu, incl, 31);
-      const int off = incl - c;
-      // adjoint: lane s owns slot s; its pairs are the targets of column s of
-      // the hit matrix, at list positions off_i + popc(hit_i below s), which
-      // increase with i
-      uint32_t col = 0u;
+      // a batch with more pairs than the list holds is processed in two
+      // halves of its slots (at most 32 x 16 pairs each)
+      const bool split = __reduce_add_sync(0xffffffffu, (unsigned)__popc(hit)) > (unsigned)kList;
       float gs[4] = {0.f, 0.f, 0.f, 0.f};
-      if (ADJ) {
-        M.hitw[lane] = hit;
-        M.offw[lane] = off;
-        col = transpose32(hit, lane);
-      }
-      {
-        uint32_t m = hit;
-        int t = off;
-        while (m) {
-          const int s = __ffs(m) - 1;
-          m &= m - 1;
-          W.list[t++] = (unsigned short)((lane << 5) | s);
+      for (int part = 0; part < (split ? 2 : 1); ++part) {
+        const uint32_t hp = split ? (hit & (part == 0 ? 0x0000ffffu : 0xffff0000u)) : hit;
+        // compaction: target-major pair list
+        const int c = __popc(hp);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
         }
-      }
-      __syncwarp();
-      for (int wb = 0; wb < T; wb += kWin) {
-        const int we = min(T, wb + kWin);
-        for (int p = wb + lane; p < we; p += 32) {
-          const int e = W.list[p];
-          float4 sg;
-          St.F[p - wb] = pair_eval(A, St, M, e >> 5, e & 31, gbase, sg);
-          if (ADJ) St.SG[p - wb] = sg;
-        }
-        __syncwarp();
-        // each target sums its own results in slot order
-        const int lo = max(off, wb), hi = min(off + c, we);
-#pragma unroll 4
-        for (int t = lo; t < hi; ++t) {
-          const float4 v = St.F[t - wb];
-          P[0] += v.x;
-          P[1] += v.y;
-          P[2] += v.z;
-          nint += (int)v.w;
-        }
+        const int T = __shfl_sync(0xffffffffu, incl, 31);
+        const int off = incl - c;
+        // adjoint: lane s owns slot s; its pairs are the targets of column s of
+        // the hit matrix, at list positions off_i + popc(hit_i below s), which
+        // increase with i
+        uint32_t col = 0u;
         if (ADJ) {
-          // source-side sums of slot `lane`, in target order
-          const uint32_t below = (1u << lane) - 1u;
-          while (col) {
-            const int i = __ffs(col) - 1;
-            const int pos = M.offw[i] + __popc(M.hitw[i] & below);
-            if (pos >= we) break;
-            const float4 v = St.SG[pos - wb];
-            gs[0] += v.x;
-            gs[1] += v.y;
-            gs[2] += v.z;
-            gs[3] += v.w;
-            col &= col - 1u;
+          M.hitw[lane] = hp;
+          M.offw[lane] = off;
+          col = transpose32(hp, lane);
+        }
+        {
+          uint32_t m = hp;
+          int t = off;
+          while (m) {
+            const int s = __ffs(m) - 1;
+            m &= m - 1;
+            W.list[t++] = (unsigned short)((lane << 5) | s);
           }
         }
         __syncwarp();
+        for (int wb = 0; wb < T; wb += kWin) {
+          const int we = min(T, wb + kWin);
+          for (int p = wb + lane; p < we; p += 32) {
+            const int e = W.list[p];
+            float4 sg;
+            St.F[p - wb] = pair_eval(A, St, M, e >> 5, e & 31, gbase, sg);
+            if (ADJ) St.SG[p - wb] = sg;
+          }
+          __syncwarp();
+          // each target sums its own results in slot order
+          const int lo = max(off, wb), hi = min(off + c, we);
+#pragma unroll 4
+          for (int t = lo; t < hi; ++t) {
+            const float4 v = St.F[t - wb];
+            P[0] += v.x;
+            P[1] += v.y;
+            P[2] += v.z;
+            nint += (int)v.w;
+          }
+          if (ADJ) {
+            // source-side sums of slot `lane`, in target order
+            const uint32_t below = (1u << lane) - 1u;
+            while (col) {
+              const int i = __ffs(col) - 1;
+              const int pos = M.offw[i] + __popc(M.hitw[i] & below);
+              if (pos >= we) break;
+              const float4 v = St.SG[pos - wb];
+              gs[0] += v.x;
+              gs[1] += v.y;
+              gs[2] += v.z;
+              gs[3] += v.w;
+              col &= col - 1u;
+            }
+          }
+          __syncwarp();
+        }
       }
       fold();
       if (ADJ && has && (gs[0] != 0.f || gs[1] != 0.f || gs[2] != 0.f || gs[3] != 0.f)) {
@@ -980,21 +985,25 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
           X.open[ix] = 0u;
         }
         __syncwarp();
-        int nd = 0;
-        for (int ix = 0; ix < nm; ++ix) {
-          const uint32_t mk = X.mask[ix];
-          if ((mk >> lane) & 1u) W.list[nd + __popc(mk & lt)] = (unsigned short)((ix << 5) | lane);
-          nd += __popc(mk);
+        // at most kList / 32 nodes per list
+        for (int m0 = 0; m0 < nm; m0 += kList / 32) {
+          const int m1 = min(nm, m0 + kList / 32);
+          int nd = 0;
+          for (int ix = m0; ix < m1; ++ix) {
+            const uint32_t mk = X.mask[ix];
+            if ((mk >> lane) & 1u) W.list[nd + __popc(mk & lt)] = (unsigned short)((ix << 5) | lane);
+            nd += __popc(mk);
+          }
+          __syncwarp();
+          for (int d = lane; d < nd; d += 32) {
+            const int e = W.list[d];
+            const int ix = e >> 5, t = e & 31;
+            const int dec = L.decide_for(A, M, t, gbase + t, X.node[ix], X.D[ix], X.C[ix], X.A[ix], X.B[ix]);
+            if (dec == DEC_ACCEPT) atomicOr(&X.acc[ix], 1u << t);
+            else if (dec == DEC_OPEN) atomicOr(&X.open[ix], 1u << t);
+          }
+          __syncwarp();
         }
-        __syncwarp();
-        for (int d = lane; d < nd; d += 32) {
-          const int e = W.list[d];
-          const int ix = e >> 5, t = e & 31;
-          const int dec = L.decide_for(A, M, t, gbase + t, X.node[ix], X.D[ix], X.C[ix], X.A[ix], X.B[ix]);
-          if (dec == DEC_ACCEPT) atomicOr(&X.acc[ix], 1u << t);
-          else if (dec == DEC_OPEN) atomicOr(&X.open[ix], 1u << t);
-        }
-        __syncwarp();
         const bool hm = lane < nm;
         const int hx = hm ? lane : 0;
         const uint32_t am = hm ? X.acc[hx] : 0u;

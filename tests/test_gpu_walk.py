@@ -152,3 +152,43 @@ def test_walk_refuses_a_failed_tree():
     with pytest.raises(m.OGError) as e:
         m.shortrange_accel(tree, w.r_s, 0.5)
     assert e.value.code == 5
+
+
+def _dense_clump(seed=77, n_clump=3000, n_bg=1000):
+    """A compact clump much smaller than r_cut in a uniform background: every
+    batch of the clump's groups has all 32 x 32 (target, source) pairs inside
+    the cut, more than the pair list holds at once."""
+    rng = np.random.default_rng(seed)
+    clump = 0.5 + rng.normal(scale=0.002, size=(n_clump, 3))
+    pos = np.concatenate([clump, rng.random((n_bg, 3))])
+    n = pos.shape[0]
+    return ics.Workload("dense_clump", pos, np.full(n, 1.0 / n), np.full(n, 1e-4), 1.0, 0.004, (0.0, 0.5, 0.9))
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.5, 0.9])
+def test_dense_clump_vs_tree(orc, theta):
+    dev = device()
+    w = _dense_clump()
+    a, tot, cnt, _ = forward(w, dev, theta)
+    ao, co = _oracle_tree(orc, w).walk(w.r_s, w.rcut, theta)
+    assert np.array_equal(cnt, co)
+    st = err_stats(a, ao)
+    print("dense clump", theta, st, "interactions", tot)
+    assert st["rms"] <= 1e-5
+
+
+def test_dense_clump_adjoint(orc):
+    dev = device()
+    m = og()
+    w = _dense_clump(seed=78)
+    wt = ics.loss_weights(w.n, 9).astype(np.float32).astype(np.float64)
+    from gpu_util import build_tree
+    tree, _, _ = build_tree(w, dev)
+    dpos, dmass = m.shortrange_adjoint(tree, w.r_s, 0.5, torch.tensor(wt, dtype=torch.float32, device=dev))
+    gp, gm = dpos.cpu().numpy(), dmass.cpu().numpy()
+    s = np.arange(0, w.n, 13)
+    op, om = _oracle_tree(orc, w).adjoint(w.r_s, w.rcut, 0.5, wt, s)
+    ep = np.abs(gp[s] - op).max() / np.abs(op).max()
+    em = np.abs(gm[s] - om).max() / np.abs(om).max()
+    print("dense clump adjoint", ep, em)
+    assert ep < 2e-5 and em < 2e-5
