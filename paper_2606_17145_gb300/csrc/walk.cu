@@ -51,7 +51,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float mi1(float t) { return t > 0.5f ? t - 1.0f : (t < -0.5f ? t + 1.0f : t); }
+// Minimum image of a box-unit difference t (|t| < 1.5): t - rint(t), with
+// rint by the 1.5 * 2^23 rounding constant (round to nearest even, so
+// +-0.5 stay), equal bit for bit to t - 1 / t + 1 / t on t > 0.5 / t < -0.5 /
+// otherwise.
+__device__ __forceinline__ float mi1(float t) {
+  const float r = __fadd_rn(__fadd_rn(t, 12582912.0f), -12582912.0f);
+  return __fadd_rn(t, -r);
+}
 
 __device__ __forceinline__ float sr_poly(float t) {
   float p = og_sr_poly[OG_SR_POLY_DEG];
@@ -189,7 +196,8 @@ constexpr int kDeep = 64;
 static_assert(kDeep + 31 + 7 * 20 + 8 <= kStack - kStackNeed, "stack bound");
 constexpr int kQueue = 128;      // queued leaves / accepted nodes per warp
 constexpr int kQueueNeed = 64;   // a step queues at most 2 entries per node
-constexpr int kSlots = 32;       // sources staged per evaluation batch
+constexpr int kSlots = 32;       // sources per evaluation batch
+constexpr int kRing = 2 * kSlots; // staged sources: two batches
 constexpr int kWin = 64;         // pair results held at once (FP32 evaluation)
 constexpr int kList = 512;       // (node or slot, target) list entries
 
@@ -208,8 +216,8 @@ struct WarpBufs {
 // Nodes of one traversal step that need per-lane decisions.
 struct MixedScratch {
   int4 D[kGroup];
-  float4 C[kGroup], A[kGroup], B[kGroup];
-  int node[kGroup];
+  float4 C[kGroup], A[kGroup], B[kGroup];  // C, A image-shifted when the node has a common image
+  int node[kGroup], fl[kGroup];
   uint32_t mask[kGroup], acc[kGroup], open[kGroup];
 };
 
@@ -342,20 +350,25 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
 }
 
 // Exact per-target decision for a node (FP32 with an FP64 re-check in the
-// band), target given by its split position.
+// band), target given by its split position.  With uni, NC and NA are
+// already shifted to the image that is the minimum image for every target
+// of the group, so no per-target minimum image is taken.
+__device__ __forceinline__ float mi1_if(bool per_target, float t) { return per_target ? mi1(t) : t; }
+
 __device__ __forceinline__ int decide_f32(const WalkArgs& A, int64_t k, const float4& th, const float4& tl, int node,
-                                          const int4& ND, const float4& NC, const float4& NA, const float4& NB) {
+                                          const int4& ND, const float4& NC, const float4& NA, const float4& NB,
+                                          bool uni) {
   const float s = NC.w, hs = 0.5f * s;
   // hi differences are exact: the minimum image is taken before the lo parts are added
-  const float ax = fabsf(mi1(NC.x - th.x) - tl.x);
-  const float ay = fabsf(mi1(NC.y - th.y) - tl.y);
-  const float az = fabsf(mi1(NC.z - th.z) - tl.z);
+  const float ax = fabsf(mi1_if(!uni, NC.x - th.x) - tl.x);
+  const float ay = fabsf(mi1_if(!uni, NC.y - th.y) - tl.y);
+  const float az = fabsf(mi1_if(!uni, NC.z - th.z) - tl.z);
   const float ex = fmaxf(ax - hs, 0.f), ey = fmaxf(ay - hs, 0.f), ez = fmaxf(az - hs, 0.f);
   const float e2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
   if (e2 > A.rc2_hi) return DEC_DISCARD;
-  const float d0 = mi1(th.x - NA.x) + (tl.x - NB.x);
-  const float d1 = mi1(th.y - NA.y) + (tl.y - NB.y);
-  const float dz = mi1(th.z - NA.z) + (tl.z - NB.z);
+  const float d0 = mi1_if(!uni, th.x - NA.x) + (tl.x - NB.x);
+  const float d1 = mi1_if(!uni, th.y - NA.y) + (tl.y - NB.y);
+  const float dz = mi1_if(!uni, th.z - NA.z) + (tl.z - NB.z);
   const float d2 = fmaf(d0, d0, fmaf(d1, d1, dz * dz));
   int dec;
   if (e2 >= A.rc2_lo) {
@@ -387,23 +400,28 @@ struct LaneF32 {
     uint32_t hitw[ADJ ? kGroup : 1];   // adjoint: each target's hit mask of the batch
     int offw[ADJ ? kGroup : 1];        // adjoint: each target's first position in the pair list
     int self[kGroup];     // staged slot holding the target itself, or -1
+    float4 Ps[kGroup];    // each target's sum over the current batch
+    int fneg[kGroup];     // listed pairs of the batch found outside the exact cut
   };
   // per-batch staging (dead between evaluations; shares memory with the
   // traversal's scratch)
+  // Staged sources live in a ring of two batches: survivors of the box test
+  // are appended at the tail, and a batch is evaluated once 32 are pending.
   struct Stage {
-    float4 sa[kSlots];    // staged source: hi part (image-shifted), mass
-    float4 sb[kSlots];    // lo part, h^2
-    int2 sc[kSlots];      // id (particle, or -2 - node), per-pair image flag
-    float fX[kSlots], fY[kSlots], fZ[kSlots], fW[kSlots];  // filter form (see stage)
-    float4 F[kWin];       // pair results of the current window (target side, hit flag)
+    float4 sa[kRing];     // staged source: hi part (image-shifted), mass
+    float4 sb[kRing];     // lo part, h^2
+    int2 sc[kRing];       // id (particle, or -2 - node), per-pair image flag
+    uint32_t sq[kRing];   // lane mask of the source's queue entry
+    float fX[kRing], fY[kRing], fZ[kRing], fW[kRing];  // filter form (see put)
     float4 SG[ADJ ? kWin : 1];  // adjoint: source-side terms of the window's pairs (G, S)
   };
-  // a slot's source, fetched one batch ahead
+  // a slot's source as read from the tree, hi part image-shifted when its
+  // entry has a common image (uni)
   struct Fetch {
     float4 a, b;
-    int id, flags;
+    int id;
     uint32_t q;
-    bool node;
+    bool node, uni;
   };
 
   int64_t k;          // sorted index of this lane's target
@@ -421,6 +439,8 @@ struct LaneF32 {
     const float4 b = A.T.pB[kc];
     M.tA[lane] = make_float4(a.x, a.y, a.z, b.w);
     M.tB[lane] = make_float4(b.x, b.y, b.z, 0.f);
+    M.Ps[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    M.fneg[lane] = 0;
     xr[0] = (a.x - G.cx) + b.x;
     xr[1] = (a.y - G.cy) + b.y;
     xr[2] = (a.z - G.cz) + b.z;
@@ -439,9 +459,9 @@ struct LaneF32 {
   }
 
   __device__ __forceinline__ int decide_for(const WalkArgs& A, const Smem& M, int t, int64_t kt, int node,
-                                            const int4& ND, const float4& NC, const float4& NA,
-                                            const float4& NB) const {
-    return decide_f32(A, kt, M.tA[t], M.tB[t], node, ND, NC, NA, NB);
+                                            const int4& ND, const float4& NC, const float4& NA, const float4& NB,
+                                            bool uni) const {
+    return decide_f32(A, kt, M.tA[t], M.tB[t], node, ND, NC, NA, NB, uni);
   }
 
   __device__ __forceinline__ Fetch fetch(const WalkArgs& A, const WarpBufs& W, int nq, int s) const {
@@ -459,49 +479,58 @@ struct LaneF32 {
       f.b = A.T.pB[j];
       f.id = j;
     }
-    f.flags = Q.w;
+    f.uni = (Q.w & 1) != 0;
+    if (f.uni) {
+      f.a.x -= shift_of(Q.w, 0);
+      f.a.y -= shift_of(Q.w, 1);
+      f.a.z -= shift_of(Q.w, 2);
+    }
     f.q = (uint32_t)Q.z;
     return f;
   }
 
-  // Stage a fetched source into batch position `lane` (or an empty slot).
+  // Position of a fetched source relative to the group centre, and whether
+  // it can have a pair inside the cut with some target of the group (its
+  // distance to the padded group box within the conservative group
+  // threshold).  Accepted nodes and entries without a common image are
+  // always kept.
+  __device__ __forceinline__ bool keep(const WalkArgs& A, const Fetch& f, const GroupInfo& G, float& x0, float& x1,
+                                       float& x2) const {
+    x0 = (f.a.x - G.cx) + f.b.x;
+    x1 = (f.a.y - G.cy) + f.b.y;
+    x2 = (f.a.z - G.cz) + f.b.z;
+    if (f.node || !f.uni) return true;
+    const float g0 = fmaxf(fabsf(x0) - G.ex, 0.f), g1 = fmaxf(fabsf(x1) - G.ey, 0.f), g2 = fmaxf(fabsf(x2) - G.ez, 0.f);
+    return fmaf(g0, g0, fmaf(g1, g1, g2 * g2)) <= A.grp_rc2;
+  }
+
+  // Stage a fetched source at ring position pos.
   // Filter form: (-2 x, -2 y, -2 z, |x|^2 - r_cut^2 - margin) relative to the
   // group centre, so |x_i - x_j|^2 - r_cut^2 - margin evaluates as
   // fW + |x_i|^2 + fX x_i + fY y_i + fZ z_i.  The FP32 evaluation of that
   // chain is within 18 u (|x_i| + |x_j|)^2 + 18 u r_cut^2 of the exact value
   // (u = 2^-24); the margin is 64 u times that bound's bracket, so every pair
   // inside the cut gives a negative value.
-  __device__ __forceinline__ void stage(const WalkArgs& A, Stage& S, Smem& M, const Fetch& f, bool has, int lane,
-                                        const GroupInfo& G, int64_t gbase, float Rg) const {
-    float4 a = f.a;
-    const float4 b = f.b;
-    const bool uni = (f.flags & 1) != 0;
-    if (uni) {
-      a.x -= shift_of(f.flags, 0);
-      a.y -= shift_of(f.flags, 1);
-      a.z -= shift_of(f.flags, 2);
+  __device__ __forceinline__ void put(const WalkArgs& A, Stage& S, Smem& M, const Fetch& f, int pos, float x0,
+                                      float x1, float x2, int64_t gbase, float Rg) const {
+    float fx = 0.f, fy = 0.f, fz = 0.f, fw = -1e30f;  // accepted node or per-pair image: always a candidate
+    if (f.uni && !f.node) {
+      const float sj = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
+      const float rr = sqrtf(sj) + Rg;
+      fx = -2.f * x0;
+      fy = -2.f * x1;
+      fz = -2.f * x2;
+      fw = (sj - A.rc2_hi) - 3.814697265625e-06f * fmaf(rr, rr, A.rc2_hi);
     }
-    float fx = 0.f, fy = 0.f, fz = 0.f, fw = 1e30f;  // empty slot: never a candidate
-    if (has) {
-      fw = -1e30f;  // accepted node or per-pair image: always a candidate
-      if (uni && !f.node) {
-        const float x0 = (a.x - G.cx) + b.x, x1 = (a.y - G.cy) + b.y, x2 = (a.z - G.cz) + b.z;
-        const float sj = fmaf(x0, x0, fmaf(x1, x1, x2 * x2));
-        const float rr = sqrtf(sj) + Rg;
-        fx = -2.f * x0;
-        fy = -2.f * x1;
-        fz = -2.f * x2;
-        fw = (sj - A.rc2_hi) - 3.814697265625e-06f * fmaf(rr, rr, A.rc2_hi);
-      }
-      S.sa[lane] = a;
-      S.sb[lane] = b;
-      S.sc[lane] = make_int2(f.id, uni ? 0 : 1);
-      if (f.id >= gbase && f.id < gbase + kGroup) M.self[f.id - gbase] = lane;
-    }
-    S.fX[lane] = fx;
-    S.fY[lane] = fy;
-    S.fZ[lane] = fz;
-    S.fW[lane] = fw;
+    S.sa[pos] = f.a;
+    S.sb[pos] = f.b;
+    S.sc[pos] = make_int2(f.id, f.uni ? 0 : 1);
+    S.sq[pos] = f.q;
+    S.fX[pos] = fx;
+    S.fY[pos] = fy;
+    S.fZ[pos] = fz;
+    S.fW[pos] = fw;
+    if (f.id >= gbase && f.id < gbase + kGroup) M.self[f.id - gbase] = pos;
   }
 
   __device__ __forceinline__ void fold() {
@@ -561,134 +590,192 @@ struct LaneF32 {
       if (lane == 0) set_status(A.wsb, ST_TREELINK);
       return;
     }
+    const uint32_t lt = (1u << lane) - 1u;
+    M.self[lane] = -1;
+    __syncwarp();
+    // raw slots are fetched 32 at a time and the survivors of the box test
+    // are appended to the ring; pending slots occupy positions
+    // [32 half, 32 half + pend) mod 64
+    int pend = 0, tail = 0, half = 0;
+    for (int rb = 0; rb < total; rb += 32) {
+      Fetch cur = {};
+      bool kp = false;
+      float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+      if (rb + lane < total) {
+        cur = fetch(A, W, nq, rb + lane);
+        kp = keep(A, cur, G, x0, x1, x2);
+      }
+      const uint32_t km = __ballot_sync(0xffffffffu, kp);
+      if (kp) put(A, St, M, cur, (tail + __popc(km & lt)) & (kRing - 1), x0, x1, x2, gbase, Rg);
+      tail = (tail + __popc(km)) & (kRing - 1);
+      pend += __popc(km);
+      __syncwarp();
+      const bool last = rb + 32 >= total;
+      while (pend >= kSlots || (last && pend > 0)) {
+        const int cnt = min(pend, kSlots);
+        batch(A, W, St, M, half * kSlots, cnt, lane, gbase, vmask);
+        pend -= cnt;
+        half ^= 1;
+      }
+    }
+  }
+
+  // One batch: the cnt staged sources at ring positions [hb, hb + cnt).
+  __device__ void batch(const WalkArgs& A, const WarpBufs& W, Stage& St, Smem& M, int hb, int cnt, int lane,
+                        int64_t gbase, uint32_t vmask) {
     const unsigned long long X2 = pack2(xr[0], xr[0]), Y2 = pack2(xr[1], xr[1]), Z2 = pack2(xr[2], xr[2]);
     const unsigned long long S2 = pack2(sr, sr);
-    Fetch nx = {};
-    if (lane < total) nx = fetch(A, W, nq, lane);
-    for (int base = 0; base < total; base += kSlots) {
-      const int cnt = min(kSlots, total - base);
-      M.self[lane] = -1;
-      __syncwarp();
-      const bool has = lane < cnt;
-      stage(A, St, M, nx, has, lane, G, gbase, Rg);
-      const uint32_t q = has ? nx.q : 0u;
-      // fetch the next batch while this one is evaluated
-      if (base + kSlots + lane < total) nx = fetch(A, W, nq, base + kSlots + lane);
-      __syncwarp();
-      // bit s of msk: slot s is in this lane's part of its entry's lane mask
-      const uint32_t cm = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
-      uint32_t msk;
-      if (__any_sync(0xffffffffu, has && q != vmask)) msk = transpose32(q, lane);
-      else msk = valid ? cm : 0u;
-      // conservative cut test for all 32 slots, two per instruction; the sign
-      // bit of each result is shifted into acc (slot 0 ends up at bit 31)
-      uint32_t acc = 0;
+    // bit s of msk: slot s is in this lane's part of its entry's lane mask
+    const bool has = lane < cnt;
+    const uint32_t q = has ? St.sq[hb + lane] : 0u;
+    const uint32_t cm = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
+    uint32_t msk;
+    if (__any_sync(0xffffffffu, has && q != vmask)) msk = transpose32(q, lane);
+    else msk = valid ? cm : 0u;
+    // conservative cut test for all 32 slots, two per instruction; the sign
+    // bit of each result is shifted into acc (slot 0 ends up at bit 31)
+    uint32_t acc = 0;
 #pragma unroll
-      for (int s = 0; s < kSlots; s += 4) {
-        const float4 fx = *reinterpret_cast<const float4*>(St.fX + s);
-        const float4 fy = *reinterpret_cast<const float4*>(St.fY + s);
-        const float4 fz = *reinterpret_cast<const float4*>(St.fZ + s);
-        const float4 fw = *reinterpret_cast<const float4*>(St.fW + s);
-        unsigned long long r01 = add2(pack2(fw.x, fw.y), S2);
-        unsigned long long r23 = add2(pack2(fw.z, fw.w), S2);
-        r01 = fma2(pack2(fz.x, fz.y), Z2, r01);
-        r23 = fma2(pack2(fz.z, fz.w), Z2, r23);
-        r01 = fma2(pack2(fy.x, fy.y), Y2, r01);
-        r23 = fma2(pack2(fy.z, fy.w), Y2, r23);
-        r01 = fma2(pack2(fx.x, fx.y), X2, r01);
-        r23 = fma2(pack2(fx.z, fx.w), X2, r23);
-        acc = __funnelshift_l((uint32_t)r01, acc, 1);
-        acc = __funnelshift_l((uint32_t)(r01 >> 32), acc, 1);
-        acc = __funnelshift_l((uint32_t)r23, acc, 1);
-        acc = __funnelshift_l((uint32_t)(r23 >> 32), acc, 1);
+    for (int s = 0; s < kSlots; s += 4) {
+      const float4 fx = *reinterpret_cast<const float4*>(St.fX + hb + s);
+      const float4 fy = *reinterpret_cast<const float4*>(St.fY + hb + s);
+      const float4 fz = *reinterpret_cast<const float4*>(St.fZ + hb + s);
+      const float4 fw = *reinterpret_cast<const float4*>(St.fW + hb + s);
+      unsigned long long r01 = add2(pack2(fw.x, fw.y), S2);
+      unsigned long long r23 = add2(pack2(fw.z, fw.w), S2);
+      r01 = fma2(pack2(fz.x, fz.y), Z2, r01);
+      r23 = fma2(pack2(fz.z, fz.w), Z2, r23);
+      r01 = fma2(pack2(fy.x, fy.y), Y2, r01);
+      r23 = fma2(pack2(fy.z, fy.w), Y2, r23);
+      r01 = fma2(pack2(fx.x, fx.y), X2, r01);
+      r23 = fma2(pack2(fx.z, fx.w), X2, r23);
+      acc = __funnelshift_l((uint32_t)r01, acc, 1);
+      acc = __funnelshift_l((uint32_t)(r01 >> 32), acc, 1);
+      acc = __funnelshift_l((uint32_t)r23, acc, 1);
+      acc = __funnelshift_l((uint32_t)(r23 >> 32), acc, 1);
+    }
+    uint32_t hit = __brev(acc) & msk;
+    const int so = M.self[lane];
+    const bool self_here = so >= hb && so < hb + cnt;
+    if (self_here) hit &= ~(1u << (so - hb));
+    // a batch with more pairs than the list holds is processed in two
+    // halves of its slots (at most 32 x 16 pairs each)
+    const bool split = __reduce_add_sync(0xffffffffu, (unsigned)__popc(hit)) > (unsigned)kList;
+    float gs[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int part = 0; part < (split ? 2 : 1); ++part) {
+      const uint32_t hp = split ? (hit & (part == 0 ? 0x0000ffffu : 0xffff0000u)) : hit;
+      // compaction: target-major pair list
+      const int c = __popc(hp);
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
-      uint32_t hit = __brev(acc) & msk;
-      const int so = M.self[lane];
-      if (so >= 0) hit &= ~(1u << so);
-      // a batch with more pairs than the list holds is processed in two
-      // halves of its slots (at most 32 x 16 pairs each)
-      const bool split = __reduce_add_sync(0xffffffffu, (unsigned)__popc(hit)) > (unsigned)kList;
-      float gs[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int part = 0; part < (split ? 2 : 1); ++part) {
-        const uint32_t hp = split ? (hit & (part == 0 ? 0x0000ffffu : 0xffff0000u)) : hit;
-        // compaction: target-major pair list
-        const int c = __popc(hp);
-        int incl = c;
+      const int T = __shfl_sync(0xffffffffu, incl, 31);
+      const int off = incl - c;
+      // adjoint: lane s owns slot s; its pairs are the targets of column s of
+      // the hit matrix, at list positions off_i + popc(hit_i below s), which
+      // increase with i
+      uint32_t col = 0u;
+      if (ADJ) {
+        M.hitw[lane] = hp;
+        M.offw[lane] = off;
+        col = transpose32(hp, lane);
+      }
+      {
+        uint32_t m = hp;
+        int t = off;
+        while (m) {
+          const int s = __ffs(m) - 1;
+          m &= m - 1;
+          W.list[t++] = (unsigned short)((lane << 5) | s);
+        }
+      }
+      nint += c;  // listed pairs; those outside the exact cut are subtracted below
+      __syncwarp();
+      for (int wb = 0; wb < T; wb += kWin) {
+        const int we = min(T, wb + kWin);
+        for (int p0 = wb; p0 < we; p0 += 32) {
+          const int p = p0 + lane;
+          const bool hv = p < we;
+          int i = 0;
+          float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (hv) {
+            const int e = W.list[p];
+            i = e >> 5;
+            float4 sg;
+            r = pair_eval(A, St, M, i, hb + (e & 31), gbase, sg);
+            if (ADJ) St.SG[p - wb] = sg;
+            if (r.w == 0.f) atomicAdd(&M.fneg[i], 1);
+          }
+          // segmented inclusive scan over the lanes: the pairs of one target
+          // are consecutive, so each target's run is summed in a fixed tree
+          // order and its last lane adds the sum to the target's batch total
+          const int oi = __shfl_sync(0xffffffffu, off, i);
+          const int ci = __shfl_sync(0xffffffffu, c, i);
+          const int first = max(oi - p0, 0);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
+          for (int d = 1; d < 32; d <<= 1) {
+            const float y0 = __shfl_up_sync(0xffffffffu, r.x, d);
+            const float y1 = __shfl_up_sync(0xffffffffu, r.y, d);
+            const float y2 = __shfl_up_sync(0xffffffffu, r.z, d);
+            if (lane - d >= first) {
+              r.x += y0;
+              r.y += y1;
+              r.z += y2;
+            }
+          }
+          if (hv && p == min(min(oi + ci, we), p0 + 32) - 1) {
+            float4 a = M.Ps[i];
+            a.x += r.x;
+            a.y += r.y;
+            a.z += r.z;
+            M.Ps[i] = a;
+          }
+          __syncwarp();
         }
-        const int T = __shfl_sync(0xffffffffu, incl, 31);
-        const int off = incl - c;
-        // adjoint: lane s owns slot s; its pairs are the targets of column s of
-        // the hit matrix, at list positions off_i + popc(hit_i below s), which
-        // increase with i
-        uint32_t col = 0u;
         if (ADJ) {
-          M.hitw[lane] = hp;
-          M.offw[lane] = off;
-          col = transpose32(hp, lane);
-        }
-        {
-          uint32_t m = hp;
-          int t = off;
-          while (m) {
-            const int s = __ffs(m) - 1;
-            m &= m - 1;
-            W.list[t++] = (unsigned short)((lane << 5) | s);
+          // source-side sums of slot `lane`, in target order
+          const uint32_t below = (1u << lane) - 1u;
+          while (col) {
+            const int i = __ffs(col) - 1;
+            const int pos = M.offw[i] + __popc(M.hitw[i] & below);
+            if (pos >= we) break;
+            const float4 v = St.SG[pos - wb];
+            gs[0] += v.x;
+            gs[1] += v.y;
+            gs[2] += v.z;
+            gs[3] += v.w;
+            col &= col - 1u;
           }
         }
         __syncwarp();
-        for (int wb = 0; wb < T; wb += kWin) {
-          const int we = min(T, wb + kWin);
-          for (int p = wb + lane; p < we; p += 32) {
-            const int e = W.list[p];
-            float4 sg;
-            St.F[p - wb] = pair_eval(A, St, M, e >> 5, e & 31, gbase, sg);
-            if (ADJ) St.SG[p - wb] = sg;
-          }
-          __syncwarp();
-          // each target sums its own results in slot order
-          const int lo = max(off, wb), hi = min(off + c, we);
-#pragma unroll 4
-          for (int t = lo; t < hi; ++t) {
-            const float4 v = St.F[t - wb];
-            P[0] += v.x;
-            P[1] += v.y;
-            P[2] += v.z;
-            nint += (int)v.w;
-          }
-          if (ADJ) {
-            // source-side sums of slot `lane`, in target order
-            const uint32_t below = (1u << lane) - 1u;
-            while (col) {
-              const int i = __ffs(col) - 1;
-              const int pos = M.offw[i] + __popc(M.hitw[i] & below);
-              if (pos >= we) break;
-              const float4 v = St.SG[pos - wb];
-              gs[0] += v.x;
-              gs[1] += v.y;
-              gs[2] += v.z;
-              gs[3] += v.w;
-              col &= col - 1u;
-            }
-          }
-          __syncwarp();
-        }
       }
-      fold();
-      if (ADJ && has && (gs[0] != 0.f || gs[1] != 0.f || gs[2] != 0.f || gs[3] != 0.f)) {
-        const int id = St.sc[lane].x;
-        double* Gd = id >= 0 ? A.Gp + 3 * (int64_t)id : A.Gn + 3 * (int64_t)(-2 - id);
-        double* Sd = id >= 0 ? A.Sp + id : A.Sn + (-2 - id);
-        atomicAdd(Gd, f2d_exact(gs[0]));
-        atomicAdd(Gd + 1, f2d_exact(gs[1]));
-        atomicAdd(Gd + 2, f2d_exact(gs[2]));
-        atomicAdd(Sd, f2d_exact(gs[3]));
-      }
-      __syncwarp();
     }
+    // this batch's sums (at most 32 terms per target) into the Kahan totals
+    {
+      const float4 ps = M.Ps[lane];
+      P[0] = ps.x;
+      P[1] = ps.y;
+      P[2] = ps.z;
+      M.Ps[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      nint -= M.fneg[lane];
+      M.fneg[lane] = 0;
+    }
+    fold();
+    if (ADJ && has && (gs[0] != 0.f || gs[1] != 0.f || gs[2] != 0.f || gs[3] != 0.f)) {
+      const int id = St.sc[hb + lane].x;
+      double* Gd = id >= 0 ? A.Gp + 3 * (int64_t)id : A.Gn + 3 * (int64_t)(-2 - id);
+      double* Sd = id >= 0 ? A.Sp + id : A.Sn + (-2 - id);
+      atomicAdd(Gd, f2d_exact(gs[0]));
+      atomicAdd(Gd + 1, f2d_exact(gs[1]));
+      atomicAdd(Gd + 2, f2d_exact(gs[2]));
+      atomicAdd(Sd, f2d_exact(gs[3]));
+    }
+    // this batch held the target's own slot
+    if (self_here) M.self[lane] = -1;
+    __syncwarp();
   }
 
   __device__ void finish(const WalkArgs& A) {
@@ -737,7 +824,8 @@ struct LaneF64 {
   }
 
   __device__ __forceinline__ int decide_for(const WalkArgs& A, const Smem&, int, int64_t kt, int node,
-                                            const int4& ND, const float4&, const float4&, const float4&) const {
+                                            const int4& ND, const float4&, const float4&, const float4&,
+                                            bool) const {
     return decide_exact(A, kt, node, meta_level(ND.w));
   }
 
@@ -975,10 +1063,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
         const int nm = __popc(mm);
         if (cls == CL_MIXED) {
           const int ix = __popc(mm & lt);
+          const int xfl = image_flags(A, G, NC);
+          float4 SC = NC, SA = NA;
+          if (xfl & 1) {
+            const float sx = shift_of(xfl, 0), sy = shift_of(xfl, 1), sz = shift_of(xfl, 2);
+            SC.x -= sx; SC.y -= sy; SC.z -= sz;
+            SA.x -= sx; SA.y -= sy; SA.z -= sz;
+          }
           X.node[ix] = node;
+          X.fl[ix] = xfl;
           X.D[ix] = ND;
-          X.C[ix] = NC;
-          X.A[ix] = NA;
+          X.C[ix] = SC;
+          X.A[ix] = SA;
           X.B[ix] = NB;
           X.mask[ix] = mask & vmask;
           X.acc[ix] = 0u;
@@ -998,7 +1094,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
           for (int d = lane; d < nd; d += 32) {
             const int e = W.list[d];
             const int ix = e >> 5, t = e & 31;
-            const int dec = L.decide_for(A, M, t, gbase + t, X.node[ix], X.D[ix], X.C[ix], X.A[ix], X.B[ix]);
+            const int dec =
+                L.decide_for(A, M, t, gbase + t, X.node[ix], X.D[ix], X.C[ix], X.A[ix], X.B[ix], (X.fl[ix] & 1) != 0);
             if (dec == DEC_ACCEPT) atomicOr(&X.acc[ix], 1u << t);
             else if (dec == DEC_OPEN) atomicOr(&X.open[ix], 1u << t);
           }
@@ -1011,7 +1108,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
         const int4 XD = X.D[hx];
         const int xnode = X.node[hx];
         const bool xleaf = meta_leaf(XD.w);
-        const int fl = (am | om) ? image_flags(A, G, X.C[hx]) : 0;
+        const int fl = X.fl[hx];
         const bool qa = am != 0u, qo = om != 0u && xleaf, po = om != 0u && !xleaf;
         const uint32_t ba = __ballot_sync(0xffffffffu, qa);
         const uint32_t bo = __ballot_sync(0xffffffffu, qo);
