@@ -61,10 +61,11 @@ def measured_peaks():
         return {}
 
 
-def walk_traffic(kernel_file="walk_fp32_zeldovich128.md"):
-    """DRAM bytes per launch of the forward walk from the committed ncu
-    summary, if it was taken on the current walk.cu (else None)."""
-    path = os.path.join(ROOT, "profiles", kernel_file)
+def walk_traffic(kernel: str, summary="walk_fp32_zeldovich128.md"):
+    """DRAM bytes per launch of a walk kernel ("forward" or "adjoint") from
+    the committed ncu summary, if it was taken on the current walk.cu (else
+    None)."""
+    path = os.path.join(ROOT, "profiles", summary)
     src = os.path.join(ROOT, "paper_2606_17145_gb300", "csrc", "walk.cu")
     try:
         text = open(path).read()
@@ -72,7 +73,7 @@ def walk_traffic(kernel_file="walk_fp32_zeldovich128.md"):
     except OSError:
         return None
     m = re.search(r"walk\.cu sha256\[:16\]:\s*([0-9a-f]+)", text)
-    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    t = re.search(r"traffic_bytes_per_launch_%s:\s*([0-9.eE+]+)" % kernel, text)
     if not m or not t or m.group(1) != digest:
         return None
     return float(t.group(1))
@@ -402,7 +403,7 @@ def main():
     dom = max(walk, key=lambda k: walk[k][0])
     dom_ms, dom_flops = walk[dom]
     achieved = interactions * dom_flops / (dom_ms * 1e-3) / 1e12
-    traffic = walk_traffic() if dom == "accel_fp32" else None
+    traffic = walk_traffic("forward" if dom == "accel_fp32" else "adjoint")
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": traffic, "kernel": dom,
                 "flops_per_interaction": dom_flops,
