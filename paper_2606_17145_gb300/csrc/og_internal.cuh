@@ -224,6 +224,9 @@ __device__ inline double div_box(double x, const BoxScale& B) {
 // Periodic wrap into [0, L]: x - L floor(x / L), each operation rounded once
 // (no fused multiply-add: the result must be bit-identical to the host form).
 __device__ inline double wrap_coord(double x, const BoxScale& B) {
+  // power-of-two side and 0 < x < L: x / L is exact and below 1, so the
+  // general form returns x itself
+  if (B.pow2 && x > 0.0 && x < B.L) return x;
   double fl = floor(div_box(x, B));
   double prod = __dmul_rn(B.L, fl);
   return __dsub_rn(x, prod);

@@ -199,33 +199,33 @@ __global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, BoxScale B)
       S2 += __shfl_xor_sync(0xffffffffu, S2, o, 8);
       H = fmax(H, __shfl_xor_sync(0xffffffffu, H, o, 8));
     }
+    // Finalisation, spread over the node's lanes: lane 0 writes the sums,
+    // mass and softening; lanes 1-3 each take one coordinate.  FP64 work
+    // costs one warp instruction however many lanes are active, so the
+    // three coordinates cost what one does.
     if (live && sub == 0) {
-      const double invM = 1.0 / M;
-      const double com[3] = {S0 * invM, S1 * invM, S2 * invM};
-      float hi[3], lo[3];
-      double cen[3];
-      float cenb[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        split_coord(com[c] * invL, hi[c], lo[c]);
-        const uint32_t q = quantise(T.x64[3 * (int64_t)D.x + c], B) >> (kMaxLevel - lev);
-        cen[c] = __dmul_rn((double)q + 0.5, side);
-        cenb[c] = ((float)q + 0.5f) * side_b;
-      }
       const double hb = H * invL;
       T.mass64[p] = M;
       T.hmax64[p] = H;
       T.S64[3 * (int64_t)p] = S0;
       T.S64[3 * (int64_t)p + 1] = S1;
       T.S64[3 * (int64_t)p + 2] = S2;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        T.com64[3 * (int64_t)p + c] = com[c];
-        T.cen64[3 * (int64_t)p + c] = cen[c];
-      }
-      T.nA[p] = make_float4(hi[0], hi[1], hi[2], (float)(M * invL2));
-      T.nB[p] = make_float4(lo[0], lo[1], lo[2], (float)(hb * hb));
-      T.nC[p] = make_float4(cenb[0], cenb[1], cenb[2], side_b);
+      reinterpret_cast<float*>(&T.nA[p])[3] = (float)(M * invL2);
+      reinterpret_cast<float*>(&T.nB[p])[3] = (float)(hb * hb);
+      reinterpret_cast<float*>(&T.nC[p])[3] = side_b;
+    }
+    if (live && sub >= 1 && sub <= 3) {
+      const int c = sub - 1;
+      const double Sc = c == 0 ? S0 : (c == 1 ? S1 : S2);
+      const double com = Sc * (1.0 / M);
+      float hi, lo;
+      split_coord(com * invL, hi, lo);
+      const uint32_t q = quantise(T.x64[3 * (int64_t)D.x + c], B) >> (kMaxLevel - lev);
+      T.com64[3 * (int64_t)p + c] = com;
+      T.cen64[3 * (int64_t)p + c] = __dmul_rn((double)q + 0.5, side);
+      reinterpret_cast<float*>(&T.nA[p])[c] = hi;
+      reinterpret_cast<float*>(&T.nB[p])[c] = lo;
+      reinterpret_cast<float*>(&T.nC[p])[c] = ((float)q + 0.5f) * side_b;
     }
   }
 }
