@@ -79,7 +79,7 @@ __device__ __forceinline__ double norm2_64(double a, double b, double c) {
 }
 
 // Exact (FP64) node decision for sorted target k.
-__device__ int decide_exact(const WalkArgs& A, int64_t k, int node, int level) {
+__device__ __noinline__ int decide_exact(const WalkArgs& A, int64_t k, int node, int level) {
   const TreeDev& T = A.T;
   const double L = A.box;
   const double side = ldexp(L, -level);
@@ -107,7 +107,7 @@ __device__ int decide_exact(const WalkArgs& A, int64_t k, int node, int level) {
   return DEC_OPEN;
 }
 
-__device__ __forceinline__ bool pair_inside_exact(const WalkArgs& A, int64_t k, int64_t j) {
+__device__ __noinline__ bool pair_inside_exact(const WalkArgs& A, int64_t k, int64_t j) {
   const double* x = A.T.x64;
   const double L = A.box;
   const double a = mi64(__dsub_rn(x[3 * k], x[3 * j]), L);
@@ -200,6 +200,7 @@ constexpr int kSlots = 32;       // sources per evaluation batch
 constexpr int kRing = 2 * kSlots; // staged sources: two batches
 constexpr int kWin = 64;         // pair results held at once (FP32 evaluation)
 constexpr int kList = 512;       // (node or slot, target) list entries
+constexpr int kMap = 512;        // slots covered by the slot -> queue entry map
 
 // Stack entry: (first node | node count << 28, lane mask); node indices stay
 // below 2^28 (checked on the host).  Queue entry: (first particle or node,
@@ -211,6 +212,7 @@ struct WarpBufs {
   int4* queue;
   int* qoff;
   unsigned short* list;  // per-lane decision list (traversal) or pair list (evaluation)
+  unsigned char* emap;   // queue entry of each slot, when the queue has at most kMap slots
 };
 
 // Nodes of one traversal step that need per-lane decisions.
@@ -219,7 +221,10 @@ struct MixedScratch {
   float4 C[kGroup], A[kGroup], B[kGroup];  // C, A image-shifted when the node has a common image
   int node[kGroup], fl[kGroup];
   uint32_t mask[kGroup], acc[kGroup], open[kGroup];
+  uint32_t dmask[kGroup];  // lanes whose sub-group box leaves the node undecided
 };
+
+constexpr int kSub = 4;  // sub-groups of 8 Hilbert-consecutive targets
 
 enum : int { CL_NONE = -1, CL_DROP = 0, CL_OPEN = 1, CL_ACCEPT = 2, CL_MIXED = 3 };
 
@@ -306,8 +311,22 @@ __device__ __forceinline__ int queue_offsets(const WalkArgs& A, const WarpBufs& 
   }
   __syncwarp();
   if (__any_sync(0xffffffffu, badq)) return -1;
+  if (run <= kMap) {
+    // slot -> entry map (entries are below kQueue <= 256)
+    for (int b0 = 0; b0 < nq; b0 += 32) {
+      const int e = b0 + lane;
+      if (e < nq) {
+        const int4 Q = W.queue[e];
+        const int c = Q.y == -1 ? 1 : Q.y;
+        const int o = W.qoff[e];
+        for (int j = 0; j < c; ++j) W.emap[o + j] = (unsigned char)e;
+      }
+    }
+    __syncwarp();
+  }
   return run;
 }
+
 
 // Queue entry holding slot s (binary search over the slot offsets).
 __device__ __forceinline__ int entry_of(const WarpBufs& W, int nq, int s) {
@@ -317,6 +336,11 @@ __device__ __forceinline__ int entry_of(const WarpBufs& W, int nq, int s) {
     if (W.qoff[mid] <= s) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// Queue entry holding slot s (total = number of slots of the queue).
+__device__ __forceinline__ int entry_lookup(const WarpBufs& W, int nq, int total, int s) {
+  return total <= kMap ? (int)W.emap[s] : entry_of(W, nq, s);
 }
 
 // 32 x 32 bit-matrix transpose across the warp: lane r holds row r (bit c =
@@ -464,9 +488,9 @@ struct LaneF32 {
     return decide_f32(A, kt, M.tA[t], M.tB[t], node, ND, NC, NA, NB, uni);
   }
 
-  __device__ __forceinline__ Fetch fetch(const WalkArgs& A, const WarpBufs& W, int nq, int s) const {
+  __device__ __forceinline__ Fetch fetch(const WalkArgs& A, const WarpBufs& W, int nq, int total, int s) const {
     Fetch f;
-    const int e = entry_of(W, nq, s);
+    const int e = entry_lookup(W, nq, total, s);
     const int4 Q = W.queue[e];
     f.node = Q.y < 0;
     if (f.node) {
@@ -602,7 +626,7 @@ struct LaneF32 {
       bool kp = false;
       float x0 = 0.f, x1 = 0.f, x2 = 0.f;
       if (rb + lane < total) {
-        cur = fetch(A, W, nq, rb + lane);
+        cur = fetch(A, W, nq, total, rb + lane);
         kp = keep(A, cur, G, x0, x1, x2);
       }
       const uint32_t km = __ballot_sync(0xffffffffu, kp);
@@ -658,10 +682,11 @@ struct LaneF32 {
     const int so = M.self[lane];
     const bool self_here = so >= hb && so < hb + cnt;
     if (self_here) hit &= ~(1u << (so - hb));
+    const int nhit = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(hit));
+    float gs[4] = {0.f, 0.f, 0.f, 0.f};
     // a batch with more pairs than the list holds is processed in two
     // halves of its slots (at most 32 x 16 pairs each)
-    const bool split = __reduce_add_sync(0xffffffffu, (unsigned)__popc(hit)) > (unsigned)kList;
-    float gs[4] = {0.f, 0.f, 0.f, 0.f};
+    const bool split = nhit > kList;
     for (int part = 0; part < (split ? 2 : 1); ++part) {
       const uint32_t hp = split ? (hit & (part == 0 ? 0x0000ffffu : 0xffff0000u)) : hit;
       // compaction: target-major pair list
@@ -756,9 +781,9 @@ struct LaneF32 {
     // this batch's sums (at most 32 terms per target) into the Kahan totals
     {
       const float4 ps = M.Ps[lane];
-      P[0] = ps.x;
-      P[1] = ps.y;
-      P[2] = ps.z;
+      P[0] += ps.x;
+      P[1] += ps.y;
+      P[2] += ps.z;
       M.Ps[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       nint -= M.fneg[lane];
       M.fneg[lane] = 0;
@@ -829,9 +854,9 @@ struct LaneF64 {
     return decide_exact(A, kt, node, meta_level(ND.w));
   }
 
-  __device__ __forceinline__ void stage(const WalkArgs& A, const WarpBufs& W, Stage& S, int nq, int s,
+  __device__ __forceinline__ void stage(const WalkArgs& A, const WarpBufs& W, Stage& S, int nq, int total, int s,
                                         int lane) const {
-    const int e = entry_of(W, nq, s);
+    const int e = entry_lookup(W, nq, total, s);
     const int4 Q = W.queue[e];
     double* d = S.slot + 6 * lane;
     int* ii = reinterpret_cast<int*>(d + 5);
@@ -894,7 +919,7 @@ struct LaneF64 {
     }
     for (int base = 0; base < total; base += kSlots) {
       const int cnt = min(kSlots, total - base);
-      if (lane < cnt) stage(A, W, St, nq, base + lane, lane);
+      if (lane < cnt) stage(A, W, St, nq, total, base + lane, lane);
       __syncwarp();
       for (int t = 0; t < cnt; ++t) pair(A, St, t, lane);
       __syncwarp();
@@ -924,8 +949,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   __shared__ int4 s_queue[kWarpsPerBlock][kQueue];
   __shared__ int s_qoff[kWarpsPerBlock][kQueue + 1];
   __shared__ unsigned short s_list[kWarpsPerBlock][kList];
+  __shared__ unsigned char s_emap[kWarpsPerBlock][kMap];
   __shared__ WarpScratch<Lane> s_scr[kWarpsPerBlock];
   __shared__ typename Lane::Smem s_lane[kWarpsPerBlock];
+  __shared__ float4 s_sgb[kWarpsPerBlock][2 * kSub];
   const TreeDev& T = A.T;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t g = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
@@ -939,6 +966,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   W.queue = s_queue[wib];
   W.qoff = s_qoff[wib];
   W.list = s_list[wib];
+  W.emap = s_emap[wib];
   MixedScratch& X = s_scr[wib].mix;
   typename Lane::Stage& St = s_scr[wib].stage;
   typename Lane::Smem& M = s_lane[wib];
@@ -962,6 +990,32 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   }
   // bound on |x_i - group centre| for the evaluation's cut filter
   const float Rg = sqrtf(fmaf(G.ex, G.ex, fmaf(G.ey, G.ey, G.ez * G.ez))) * 1.0001f + 1e-6f;
+  // boxes of the 4 sub-groups of 8 targets (box units, padded outward by
+  // more than the FP32 rounding of a position in [0, 1))
+  float4* SGB = s_sgb[wib];
+  {
+    const float4 pa = T.pA[valid ? k : 0], pb = T.pB[valid ? k : 0];
+    float lo[3] = {pa.x + pb.x, pa.y + pb.y, pa.z + pb.z};
+    float hi[3] = {lo[0], lo[1], lo[2]};
+    if (!valid) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { lo[c] = 1e30f; hi[c] = -1e30f; }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+        hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+      }
+    if ((lane & 7) == 0) {
+      const float pad = 2e-7f;
+      SGB[2 * (lane >> 3)] = make_float4(0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2]), 0.f);
+      SGB[2 * (lane >> 3) + 1] = make_float4(0.5f * (hi[0] - lo[0]) * 1.0001f + pad,
+                                             0.5f * (hi[1] - lo[1]) * 1.0001f + pad,
+                                             0.5f * (hi[2] - lo[2]) * 1.0001f + pad, 0.f);
+    }
+  }
 
   Lane L;
   L.init(A, M, k, valid, lane, G);
@@ -1079,6 +1133,24 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
           X.mask[ix] = mask & vmask;
           X.acc[ix] = 0u;
           X.open[ix] = 0u;
+          X.dmask[ix] = 0u;
+        }
+        __syncwarp();
+        // each (node, sub-group) pair is first classified against the
+        // sub-group's box; only undecided sub-groups need per-lane decisions
+        for (int j = lane; j < kSub * nm; j += 32) {
+          const int ix = j >> 2, g = j & 3;
+          const uint32_t gm = X.mask[ix] & (0xffu << (8 * g));
+          if (gm) {
+            const float4 c4 = SGB[2 * g], e4 = SGB[2 * g + 1];
+            GroupInfo Gs;
+            Gs.cx = c4.x; Gs.cy = c4.y; Gs.cz = c4.z;
+            Gs.ex = e4.x; Gs.ey = e4.y; Gs.ez = e4.z;
+            const int cg = classify(A, Gs, X.C[ix], X.A[ix], X.B[ix]);
+            if (cg == CL_OPEN) atomicOr(&X.open[ix], gm);
+            else if (cg == CL_ACCEPT) atomicOr(&X.acc[ix], gm);
+            else if (cg == CL_MIXED) atomicOr(&X.dmask[ix], gm);
+          }
         }
         __syncwarp();
         // at most kList / 32 nodes per list
@@ -1086,7 +1158,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
           const int m1 = min(nm, m0 + kList / 32);
           int nd = 0;
           for (int ix = m0; ix < m1; ++ix) {
-            const uint32_t mk = X.mask[ix];
+            const uint32_t mk = X.dmask[ix];
             if ((mk >> lane) & 1u) W.list[nd + __popc(mk & lt)] = (unsigned short)((ix << 5) | lane);
             nd += __popc(mk);
           }
