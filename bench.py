@@ -61,6 +61,22 @@ def measured_peaks():
         return {}
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest value of x over the ranks (x itself on one rank): the
+    replicas' time is that of the slowest one."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ws: int, ms: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank in ms."""
+    return ws * units_per_rank / (ms * 1e-3)
+
+
 def walk_traffic(kernel: str, summary="walk_fp32_zeldovich128.md"):
     """DRAM bytes per launch of a walk kernel ("forward" or "adjoint") from
     the committed ncu summary, if it was taken on the current walk.cu (else
@@ -325,12 +341,8 @@ def main():
         for i, k in enumerate(phases):
             per[k].append(ev[i].elapsed_time(ev[i + 1]))
     clocks = clk.summary()
-    ms = sum(step_ms) / len(step_ms)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * interactions / (ms * 1e-3)
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), ws, dev)
+    value = job_rate(interactions, ws, ms)
     pms = {k: sum(v) / len(v) for k, v in per.items()}
 
     # FP64 walk on the same tree (comparison variant)
@@ -388,11 +400,7 @@ def main():
         b.record()
         torch.cuda.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e_mean = sum(e2e_ms) / len(e2e_ms)
-    if ws > 1:
-        t = torch.tensor([e2e_mean], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_mean = float(t.item())
+    e2e_mean = max_over_ranks(sum(e2e_ms) / len(e2e_ms), ws, dev)
 
     # roofline of the dominant kernel (FP32 ALU bound; peak from unit counts and the max SM clock)
     peaks = measured_peaks()
@@ -422,7 +430,7 @@ def main():
                    "l2": "flushed by a 256 MiB write between timed steps", "parallelism": f"replicas x{ws}",
                    "launch": "CUDA graph replay of the whole step" if graph is not None else "stream launches"},
         "clocks": clocks,
-        "e2e": {"value": ws * interactions / (e2e_mean * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(interactions, ws, e2e_mean), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
         "gpu_launches": per_step_launches * args.steps,
         "roofline": roofline,
