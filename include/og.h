@@ -70,7 +70,8 @@ typedef enum og_precision {
  * max_walk_iters 0 (= 2^24 node visits per 32-particle group). */
 typedef struct og_params {
   int32_t leaf_size;       /* B: a node with more than B particles is split (1..32) */
-  int32_t reserved0;
+  int32_t deep_stack;      /* walk stack depth above which a step pops a single child range: 0 = 64, the
+                              largest allowed; a smaller value only trades speed for a lower stack */
   double rcut_factor;      /* rcut = rcut_factor * r_s */
   int64_t node_capacity;   /* nodes reserved in the tree buffer */
   int64_t max_walk_iters;  /* node-visit cap per group; exceeding it sets OG_EWALK */
@@ -92,6 +93,8 @@ typedef struct og_tree {
   void* mem;               /* device buffer (starts with the status block) */
   size_t mem_bytes;
   int64_t max_walk_iters;
+  int32_t deep_stack;      /* from og_params (0 replaced by 64) */
+  int32_t reserved1;
 } og_tree;
 
 /* Bytes of workspace og_keys_sort needs for n particles. */

@@ -77,13 +77,14 @@ def _workspace(nbytes: int, device) -> torch.Tensor:
 
 
 def params(leaf_size: int = 8, rcut_factor: float = 4.5, node_capacity: int = 0,
-           max_walk_iters: int = 0) -> N.og_params:
+           max_walk_iters: int = 0, deep_stack: int = 0) -> N.og_params:
     p = N.og_params()
     lib().og_params_default(C.byref(p))
     p.leaf_size = leaf_size
     p.rcut_factor = rcut_factor
     p.node_capacity = node_capacity
     p.max_walk_iters = max_walk_iters
+    p.deep_stack = deep_stack
     return p
 
 

@@ -15,14 +15,15 @@ OG_FP32_KAHAN, OG_FP64 = 0, 1
 
 
 class og_params(C.Structure):
-    _fields_ = [("leaf_size", C.c_int32), ("reserved0", C.c_int32), ("rcut_factor", C.c_double),
+    _fields_ = [("leaf_size", C.c_int32), ("deep_stack", C.c_int32), ("rcut_factor", C.c_double),
                 ("node_capacity", C.c_int64), ("max_walk_iters", C.c_int64)]
 
 
 class og_tree(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_groups", C.c_int64), ("node_capacity", C.c_int64), ("box", C.c_double),
                 ("rcut_factor", C.c_double), ("leaf_size", C.c_int32), ("built", C.c_int32),
-                ("mem", C.c_void_p), ("mem_bytes", C.c_size_t), ("max_walk_iters", C.c_int64)]
+                ("mem", C.c_void_p), ("mem_bytes", C.c_size_t), ("max_walk_iters", C.c_int64),
+                ("deep_stack", C.c_int32), ("reserved1", C.c_int32)]
 
 
 # symbol -> (restype, argtypes)

@@ -86,6 +86,7 @@ og_status og_tree_build(const uint64_t* keys_sorted, const int32_t* order, const
   if (q.leaf_size < 1 || q.leaf_size > 32) return OG_EINVAL;
   if (!finite_pos(q.rcut_factor)) return OG_EINVAL;
   if (q.node_capacity < 0 || q.max_walk_iters < 0) return OG_EINVAL;
+  if (q.deep_stack < 0 || q.deep_stack > 64) return OG_EINVAL;
   const int64_t cap = q.node_capacity > 0 ? q.node_capacity : default_capacity(n);
   if (cap > kMaxN) return OG_EINVAL;
   if (!aligned(tree_mem)) return OG_EINVAL;
@@ -102,6 +103,7 @@ og_status og_tree_build(const uint64_t* keys_sorted, const int32_t* order, const
   t.mem = tree_mem;
   t.mem_bytes = tree_bytes;
   t.max_walk_iters = q.max_walk_iters > 0 ? q.max_walk_iters : (1LL << 24);
+  t.deep_stack = q.deep_stack > 0 ? q.deep_stack : 64;
   BuildArgs A;
   A.T = tree_view(&t);
   A.keys = keys_sorted;
@@ -131,6 +133,8 @@ static og_status walk_common(const og_tree* t, double r_s, double theta, WalkArg
   std::memset(&A, 0, sizeof(A));
   A.T = tree_view(t);
   A.max_iters = t->max_walk_iters;
+  if (t->deep_stack < 1 || t->deep_stack > 64) return OG_EINVAL;
+  A.deep = t->deep_stack;
   const double rcb = rcut / L;
   const double rcb2 = rcb * rcb;
   const double nb = std::fmax(kNodeBand, 2e-6 / rcb);

@@ -1034,7 +1034,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
       // (one range when the stack is deep).  The index is clamped so no lane
       // forms an address outside the stack, and every pop completes before
       // any push.
-      const int m = sp > kDeep ? 1 : min(sp, 32);
+      const int m = sp > min(A.deep, kDeep) ? 1 : min(sp, 32);
       const int2 E = W.stack[max(sp - 1 - lane, 0)];
       __syncwarp();
       const uint32_t ex = (uint32_t)E.x;

@@ -56,6 +56,11 @@ def test_host_argument_checks(L):
     assert L.og_tree_build(ws, ws, ws, ws, None, 0.1, 10, 1.0, C.byref(p), ws, 1 << 30, C.byref(hdr),
                            None) == N.OG_EINVAL
     L.og_params_default(C.byref(p))
+    for bad in (-1, 65):
+        p.deep_stack = bad
+        assert L.og_tree_build(ws, ws, ws, ws, None, 0.1, 10, 1.0, C.byref(p), ws, 1 << 30, C.byref(hdr),
+                               None) == N.OG_EINVAL
+    L.og_params_default(C.byref(p))
     assert L.og_tree_build(ws, ws, ws, ws, None, 0.1, 10, 1.0, C.byref(p), ws, 64, C.byref(hdr),
                            None) == N.OG_ENOSPACE
     # walks on a header that was never built

@@ -192,3 +192,30 @@ def test_dense_clump_adjoint(orc):
     em = np.abs(gm[s] - om).max() / np.abs(om).max()
     print("dense clump adjoint", ep, em)
     assert ep < 2e-5 and em < 2e-5
+
+
+@pytest.mark.parametrize("name,scale,deep", [("nfw256", 24, 1), ("zoom8m", 20000, 3), ("uniform4096", None, 2)])
+def test_single_range_pops_vs_tree(orc, name, scale, deep):
+    """With the deep-stack threshold lowered, most traversal steps pop a
+    single child range; the terms must stay exactly the per-target walk's."""
+    dev = device()
+    w = ics.make(name, scale) if scale else ics.make(name)
+    a, tot, cnt, _ = forward(w, dev, 0.5, deep_stack=deep)
+    ao, co = _oracle_tree(orc, w).walk(w.r_s, w.rcut, 0.5)
+    assert np.array_equal(cnt, co)
+    assert err_stats(a, ao)["rms"] <= 1e-5
+
+
+def test_single_range_pops_adjoint(orc):
+    dev = device()
+    m = og()
+    w = _dense_clump(seed=79, n_clump=1500, n_bg=1500)
+    wt = ics.loss_weights(w.n, 10).astype(np.float32).astype(np.float64)
+    from gpu_util import build_tree
+    tree, _, _ = build_tree(w, dev, deep_stack=1)
+    dpos, dmass = m.shortrange_adjoint(tree, w.r_s, 0.5, torch.tensor(wt, dtype=torch.float32, device=dev))
+    gp, gm = dpos.cpu().numpy(), dmass.cpu().numpy()
+    s = np.arange(0, w.n, 11)
+    op, om = _oracle_tree(orc, w).adjoint(w.r_s, w.rcut, 0.5, wt, s)
+    assert np.abs(gp[s] - op).max() / np.abs(op).max() < 2e-5
+    assert np.abs(gm[s] - om).max() / np.abs(om).max() < 2e-5
