@@ -198,7 +198,6 @@ constexpr int kQueue = 128;      // queued leaves / accepted nodes per warp
 constexpr int kQueueNeed = 64;   // a step queues at most 2 entries per node
 constexpr int kSlots = 32;       // sources per evaluation batch
 constexpr int kRing = 2 * kSlots; // staged sources: two batches
-constexpr int kWin = 64;         // pair results held at once (FP32 evaluation)
 constexpr int kList = 512;       // (node or slot, target) list entries
 constexpr int kMap = 512;        // slots covered by the slot -> queue entry map
 
@@ -421,8 +420,7 @@ struct LaneF32 {
     float4 tA[kGroup];    // targets: hi part, h^2
     float4 tB[kGroup];    // targets: lo part
     float4 tW[ADJ ? kGroup : 1];   // adjoint: dL/da of each target
-    uint32_t hitw[ADJ ? kGroup : 1];   // adjoint: each target's hit mask of the batch
-    int offw[ADJ ? kGroup : 1];        // adjoint: each target's first position in the pair list
+    float4 GS[ADJ ? kSlots : 1];  // adjoint: each slot's source-side sums (G, S) over the batch
     int self[kGroup];     // staged slot holding the target itself, or -1
     float4 Ps[kGroup];    // each target's sum over the current batch
     int fneg[kGroup];     // listed pairs of the batch found outside the exact cut
@@ -437,7 +435,6 @@ struct LaneF32 {
     int2 sc[kRing];       // id (particle, or -2 - node), per-pair image flag
     uint32_t sq[kRing];   // lane mask of the source's queue entry
     float fX[kRing], fY[kRing], fZ[kRing], fW[kRing];  // filter form (see put)
-    float4 SG[ADJ ? kWin : 1];  // adjoint: source-side terms of the window's pairs (G, S)
   };
   // a slot's source as read from the tree, hi part image-shifted when its
   // entry has a common image (uni)
@@ -465,6 +462,7 @@ struct LaneF32 {
     M.tB[lane] = make_float4(b.x, b.y, b.z, 0.f);
     M.Ps[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     M.fneg[lane] = 0;
+    if (ADJ) M.GS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     xr[0] = (a.x - G.cx) + b.x;
     xr[1] = (a.y - G.cy) + b.y;
     xr[2] = (a.z - G.cz) + b.z;
@@ -683,7 +681,6 @@ struct LaneF32 {
     const bool self_here = so >= hb && so < hb + cnt;
     if (self_here) hit &= ~(1u << (so - hb));
     const int nhit = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(hit));
-    float gs[4] = {0.f, 0.f, 0.f, 0.f};
     // a batch with more pairs than the list holds is processed in two
     // halves of its slots (at most 32 x 16 pairs each)
     const bool split = nhit > kList;
@@ -699,15 +696,6 @@ struct LaneF32 {
       }
       const int T = __shfl_sync(0xffffffffu, incl, 31);
       const int off = incl - c;
-      // adjoint: lane s owns slot s; its pairs are the targets of column s of
-      // the hit matrix, at list positions off_i + popc(hit_i below s), which
-      // increase with i
-      uint32_t col = 0u;
-      if (ADJ) {
-        M.hitw[lane] = hp;
-        M.offw[lane] = off;
-        col = transpose32(hp, lane);
-      }
       {
         uint32_t m = hp;
         int t = off;
@@ -719,19 +707,19 @@ struct LaneF32 {
       }
       nint += c;  // listed pairs; those outside the exact cut are subtracted below
       __syncwarp();
-      for (int wb = 0; wb < T; wb += kWin) {
-        const int we = min(T, wb + kWin);
-        for (int p0 = wb; p0 < we; p0 += 32) {
+      {
+        const int we = T;
+        for (int p0 = 0; p0 < we; p0 += 32) {
           const int p = p0 + lane;
           const bool hv = p < we;
-          int i = 0;
+          int i = 0, slot = 0;
           float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+          float4 sg = make_float4(0.f, 0.f, 0.f, 0.f);
           if (hv) {
             const int e = W.list[p];
             i = e >> 5;
-            float4 sg;
-            r = pair_eval(A, St, M, i, hb + (e & 31), gbase, sg);
-            if (ADJ) St.SG[p - wb] = sg;
+            slot = e & 31;
+            r = pair_eval(A, St, M, i, hb + slot, gbase, sg);
             if (r.w == 0.f) atomicAdd(&M.fneg[i], 1);
           }
           // segmented inclusive scan over the lanes: the pairs of one target
@@ -758,22 +746,38 @@ struct LaneF32 {
             a.z += r.z;
             M.Ps[i] = a;
           }
-          __syncwarp();
-        }
-        if (ADJ) {
-          // source-side sums of slot `lane`, in target order
-          const uint32_t below = (1u << lane) - 1u;
-          while (col) {
-            const int i = __ffs(col) - 1;
-            const int pos = M.offw[i] + __popc(M.hitw[i] & below);
-            if (pos >= we) break;
-            const float4 v = St.SG[pos - wb];
-            gs[0] += v.x;
-            gs[1] += v.y;
-            gs[2] += v.z;
-            gs[3] += v.w;
-            col &= col - 1u;
+          if (ADJ) {
+            // source-side terms: the lanes holding the same slot are summed
+            // in lane order onto the lowest of them, which adds the sum to
+            // the slot's batch total (one writer per slot per iteration)
+            const uint32_t grp = __match_any_sync(0xffffffffu, hv ? slot : 32 + lane);
+            const int gmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(grp));
+            uint32_t rest = grp & (grp - 1u);
+            float4 acc = sg;
+            for (int k = 1; k < gmax; ++k) {
+              const int src = rest ? __ffs(rest) - 1 : lane;
+              const float v0 = __shfl_sync(0xffffffffu, sg.x, src);
+              const float v1 = __shfl_sync(0xffffffffu, sg.y, src);
+              const float v2 = __shfl_sync(0xffffffffu, sg.z, src);
+              const float v3 = __shfl_sync(0xffffffffu, sg.w, src);
+              if (rest) {
+                acc.x += v0;
+                acc.y += v1;
+                acc.z += v2;
+                acc.w += v3;
+                rest &= rest - 1u;
+              }
+            }
+            if (hv && lane == __ffs(grp) - 1) {
+              float4 g = M.GS[slot];
+              g.x += acc.x;
+              g.y += acc.y;
+              g.z += acc.z;
+              g.w += acc.w;
+              M.GS[slot] = g;
+            }
           }
+          __syncwarp();
         }
         __syncwarp();
       }
@@ -789,14 +793,18 @@ struct LaneF32 {
       M.fneg[lane] = 0;
     }
     fold();
-    if (ADJ && has && (gs[0] != 0.f || gs[1] != 0.f || gs[2] != 0.f || gs[3] != 0.f)) {
-      const int id = St.sc[hb + lane].x;
-      double* Gd = id >= 0 ? A.Gp + 3 * (int64_t)id : A.Gn + 3 * (int64_t)(-2 - id);
-      double* Sd = id >= 0 ? A.Sp + id : A.Sn + (-2 - id);
-      atomicAdd(Gd, f2d_exact(gs[0]));
-      atomicAdd(Gd + 1, f2d_exact(gs[1]));
-      atomicAdd(Gd + 2, f2d_exact(gs[2]));
-      atomicAdd(Sd, f2d_exact(gs[3]));
+    if (ADJ) {
+      const float4 g = M.GS[lane];
+      if (has && (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f)) {
+        const int id = St.sc[hb + lane].x;
+        double* Gd = id >= 0 ? A.Gp + 3 * (int64_t)id : A.Gn + 3 * (int64_t)(-2 - id);
+        double* Sd = id >= 0 ? A.Sp + id : A.Sn + (-2 - id);
+        atomicAdd(Gd, f2d_exact(g.x));
+        atomicAdd(Gd + 1, f2d_exact(g.y));
+        atomicAdd(Gd + 2, f2d_exact(g.z));
+        atomicAdd(Sd, f2d_exact(g.w));
+      }
+      M.GS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // this batch held the target's own slot
     if (self_here) M.self[lane] = -1;
