@@ -29,6 +29,8 @@
 // special-function unit (rsqrt, ex2) and a polynomial for
 // erfcx(u) + 2u/sqrt(pi); per-target sums are Kahan-compensated after every
 // batch of 32 staged sources (at most 32 terms per target).
+#include <type_traits>
+
 #include "og_internal.cuh"
 #include "short_range_poly.inc"
 
@@ -412,9 +414,18 @@ __device__ __forceinline__ int decide_f32(const WalkArgs& A, int64_t k, const fl
   return dec;
 }
 
-// FP32 lane: forward (ADJ = false) or adjoint (ADJ = true).
-template <bool ADJ>
-struct LaneF32 {
+// One pair's result on the target side: FP32 (with the hit flag in w) or
+// FP64 (hit flag separate).
+template <bool F64> struct Term { float x, y, z, w; };
+template <> struct Term<true> { double x, y, z; float w; };
+
+// Lane of the walk: FP32 + Kahan forward (ADJ = false) or adjoint
+// (ADJ = true), or the all-FP64 forward comparison variant (F64 = true:
+// FP64 decisions, FP64 pair arithmetic with CUDA's erfc / exp, plain double
+// sums).  All share the traversal, the box test, the FP32 cut filter (a
+// conservative superset of the pairs inside the cut) and the compaction.
+template <bool ADJ, bool F64>
+struct LaneFP {
   // per-warp data that lives through the whole walk
   struct Smem {
     float4 tA[kGroup];    // targets: hi part, h^2
@@ -422,7 +433,7 @@ struct LaneF32 {
     float4 tW[ADJ ? kGroup : 1];   // adjoint: dL/da of each target
     float4 GS[ADJ ? kSlots : 1];  // adjoint: each slot's source-side sums (G, S) over the batch
     int self[kGroup];     // staged slot holding the target itself, or -1
-    float4 Ps[kGroup];    // each target's sum over the current batch
+    typename std::conditional<F64, double3, float4>::type Ps[kGroup];  // each target's sum over the batch
     int fneg[kGroup];     // listed pairs of the batch found outside the exact cut
   };
   // per-batch staging (dead between evaluations; shares memory with the
@@ -450,6 +461,7 @@ struct LaneF32 {
   float xr[3], sr;    // position relative to the group centre and its square (filter)
   float P[3];         // partial sum since the last fold
   float S[3], C[3];   // Kahan total and compensation
+  double a64[3];      // FP64 variant: plain double sums
   int nint;
 
   __device__ void init(const WalkArgs& A, Smem& M, int64_t kk, bool v, int lane, const GroupInfo& G) {
@@ -460,7 +472,9 @@ struct LaneF32 {
     const float4 b = A.T.pB[kc];
     M.tA[lane] = make_float4(a.x, a.y, a.z, b.w);
     M.tB[lane] = make_float4(b.x, b.y, b.z, 0.f);
-    M.Ps[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (F64) M.Ps[lane] = make_double3(0.0, 0.0, 0.0);
+    else M.Ps[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    a64[0] = a64[1] = a64[2] = 0.0;
     M.fneg[lane] = 0;
     if (ADJ) M.GS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     xr[0] = (a.x - G.cx) + b.x;
@@ -483,7 +497,58 @@ struct LaneF32 {
   __device__ __forceinline__ int decide_for(const WalkArgs& A, const Smem& M, int t, int64_t kt, int node,
                                             const int4& ND, const float4& NC, const float4& NA, const float4& NB,
                                             bool uni) const {
-    return decide_f32(A, kt, M.tA[t], M.tB[t], node, ND, NC, NA, NB, uni);
+    if constexpr (F64) return decide_exact(A, kt, node, meta_level(ND.w));
+    else return decide_f32(A, kt, M.tA[t], M.tB[t], node, ND, NC, NA, NB, uni);
+  }
+
+  // FP64 variant: target gbase + i against staged slot s, read from the
+  // FP64 tree arrays; the cut is taken on the FP64 distance (accepted nodes
+  // are inside by decision).
+  __device__ __forceinline__ Term<true> pair_eval64(const WalkArgs& A, const Stage& St, int i, int s,
+                                                    int64_t gbase) const {
+    const int id = St.sc[s].x;
+    const int64_t kt = gbase + i;
+    const double* x = A.T.x64;
+    double sp[3], m, h;
+    if (id >= 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sp[c] = x[3 * (int64_t)id + c];
+      m = A.T.m64[id];
+      h = A.T.h64[id];
+    } else {
+      const int64_t n = -2 - id;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sp[c] = A.T.com64[3 * n + c];
+      m = A.T.mass64[n];
+      h = A.T.hmax64[n];
+    }
+    double dv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dv[c] = mi64(__dsub_rn(x[3 * kt + c], sp[c]), A.box);
+    const double r2 = norm2_64(dv[0], dv[1], dv[2]);
+    Term<true> t;
+    t.x = t.y = t.z = 0.0;
+    t.w = 0.f;
+    if (id >= 0 && !(r2 < A.rc2_64)) return t;
+    const double r = sqrt(r2);
+    const double hh = fmax(A.T.h64[kt], h);
+    double K;
+    if (r >= hh) {
+      K = 1.0 / (r * r * r);
+    } else {
+      const double v = r / hh;
+      const double h3 = 1.0 / (hh * hh * hh);
+      if (v < 0.5) K = h3 * (32.0 / 3.0 + v * v * (32.0 * v - 38.4));
+      else K = h3 * (64.0 / 3.0 - 48.0 * v + 38.4 * v * v - (32.0 / 3.0) * v * v * v - (1.0 / 15.0) / (v * v * v));
+    }
+    const double u = r * A.inv2rs64;
+    const double f = erfc(u) + 1.1283791670955126 * u * exp(-u * u);
+    const double sc = -m * K * f;
+    t.x = sc * dv[0];
+    t.y = sc * dv[1];
+    t.z = sc * dv[2];
+    t.w = 1.f;
+    return t;
   }
 
   __device__ __forceinline__ Fetch fetch(const WalkArgs& A, const WarpBufs& W, int nq, int total, int s) const {
@@ -713,13 +778,23 @@ struct LaneF32 {
           const int p = p0 + lane;
           const bool hv = p < we;
           int i = 0, slot = 0;
-          float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+          Term<F64> r;
+          r.x = r.y = r.z = 0;
+          r.w = 0.f;
           float4 sg = make_float4(0.f, 0.f, 0.f, 0.f);
           if (hv) {
             const int e = W.list[p];
             i = e >> 5;
             slot = e & 31;
-            r = pair_eval(A, St, M, i, hb + slot, gbase, sg);
+            if constexpr (F64) {
+              r = pair_eval64(A, St, i, hb + slot, gbase);
+            } else {
+              const float4 rr = pair_eval(A, St, M, i, hb + slot, gbase, sg);
+              r.x = rr.x;
+              r.y = rr.y;
+              r.z = rr.z;
+              r.w = rr.w;
+            }
             if (r.w == 0.f) atomicAdd(&M.fneg[i], 1);
           }
           // segmented inclusive scan over the lanes: the pairs of one target
@@ -730,9 +805,9 @@ struct LaneF32 {
           const int first = max(oi - p0, 0);
 #pragma unroll
           for (int d = 1; d < 32; d <<= 1) {
-            const float y0 = __shfl_up_sync(0xffffffffu, r.x, d);
-            const float y1 = __shfl_up_sync(0xffffffffu, r.y, d);
-            const float y2 = __shfl_up_sync(0xffffffffu, r.z, d);
+            const auto y0 = __shfl_up_sync(0xffffffffu, r.x, d);
+            const auto y1 = __shfl_up_sync(0xffffffffu, r.y, d);
+            const auto y2 = __shfl_up_sync(0xffffffffu, r.z, d);
             if (lane - d >= first) {
               r.x += y0;
               r.y += y1;
@@ -740,7 +815,7 @@ struct LaneF32 {
             }
           }
           if (hv && p == min(min(oi + ci, we), p0 + 32) - 1) {
-            float4 a = M.Ps[i];
+            auto a = M.Ps[i];
             a.x += r.x;
             a.y += r.y;
             a.z += r.z;
@@ -783,16 +858,24 @@ struct LaneF32 {
       }
     }
     // this batch's sums (at most 32 terms per target) into the Kahan totals
+    // (FP64 variant: into the plain double sums)
     {
-      const float4 ps = M.Ps[lane];
-      P[0] += ps.x;
-      P[1] += ps.y;
-      P[2] += ps.z;
-      M.Ps[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const auto ps = M.Ps[lane];
+      if constexpr (F64) {
+        a64[0] += ps.x;
+        a64[1] += ps.y;
+        a64[2] += ps.z;
+        M.Ps[lane] = make_double3(0.0, 0.0, 0.0);
+      } else {
+        P[0] += ps.x;
+        P[1] += ps.y;
+        P[2] += ps.z;
+        M.Ps[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       nint -= M.fneg[lane];
       M.fneg[lane] = 0;
     }
-    fold();
+    if constexpr (!F64) fold();
     if (ADJ) {
       const float4 g = M.GS[lane];
       if (has && (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f)) {
@@ -814,7 +897,11 @@ struct LaneF32 {
   __device__ void finish(const WalkArgs& A) {
     if (!valid) return;
     const int32_t i = A.T.order[k];
-    if (!ADJ) {
+    if (F64) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) A.accd[3 * (int64_t)i + c] = a64[c];
+      if (A.counts) A.counts[i] = nint;
+    } else if (!ADJ) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) A.accf[3 * (int64_t)i + c] = S[c] - C[c];
       if (A.counts) A.counts[i] = nint;
@@ -825,123 +912,9 @@ struct LaneF32 {
   }
 };
 
-// FP64 lane (forward only): the same traversal and decisions, double-precision
-// interactions with the library's erfc / exp, plain double sums; every lane
-// evaluates every staged slot in lockstep.
-struct LaneF64 {
-  struct Smem {
-    int unused;
-  };
-  struct Stage {
-    double slot[kSlots * 6];  // per slot: double x, y, z, m, h; int id, int lane mask
-  };
-
-  int64_t k;
-  bool valid;
-  double x[3];
-  double h;
-  double a[3];
-  int nint;
-
-  __device__ void init(const WalkArgs& A, Smem&, int64_t kk, bool v, int, const GroupInfo&) {
-    k = kk;
-    valid = v;
-    const int64_t kc = v ? kk : 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      x[c] = A.T.x64[3 * kc + c];
-      a[c] = 0.0;
-    }
-    h = A.T.h64[kc];
-    nint = 0;
-  }
-
-  __device__ __forceinline__ int decide_for(const WalkArgs& A, const Smem&, int, int64_t kt, int node,
-                                            const int4& ND, const float4&, const float4&, const float4&,
-                                            bool) const {
-    return decide_exact(A, kt, node, meta_level(ND.w));
-  }
-
-  __device__ __forceinline__ void stage(const WalkArgs& A, const WarpBufs& W, Stage& S, int nq, int total, int s,
-                                        int lane) const {
-    const int e = entry_lookup(W, nq, total, s);
-    const int4 Q = W.queue[e];
-    double* d = S.slot + 6 * lane;
-    int* ii = reinterpret_cast<int*>(d + 5);
-    if (Q.y < 0) {
-      const int n = Q.x;
-      d[0] = A.T.com64[3 * (int64_t)n];
-      d[1] = A.T.com64[3 * (int64_t)n + 1];
-      d[2] = A.T.com64[3 * (int64_t)n + 2];
-      d[3] = A.T.mass64[n];
-      d[4] = A.T.hmax64[n];
-      ii[0] = -2 - n;
-    } else {
-      const int j = Q.x + (s - W.qoff[e]);
-      d[0] = A.T.x64[3 * (int64_t)j];
-      d[1] = A.T.x64[3 * (int64_t)j + 1];
-      d[2] = A.T.x64[3 * (int64_t)j + 2];
-      d[3] = A.T.m64[j];
-      d[4] = A.T.h64[j];
-      ii[0] = j;
-    }
-    ii[1] = Q.z;
-  }
-
-  __device__ __forceinline__ void pair(const WalkArgs& A, const Stage& S, int t, int lane) {
-    const double* d = S.slot + 6 * t;
-    const int* ii = reinterpret_cast<const int*>(d + 5);
-    const int id = ii[0];
-    const bool mine = valid && ((ii[1] >> lane) & 1) && id != k;
-    if (!mine) return;
-    double dv[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) dv[c] = mi64(__dsub_rn(x[c], d[c]), A.box);
-    const double r2 = norm2_64(dv[0], dv[1], dv[2]);
-    if (id >= 0 && !(r2 < A.rc2_64)) return;
-    const double r = sqrt(r2);
-    const double hh = fmax(h, d[4]);
-    double K;
-    if (r >= hh) {
-      K = 1.0 / (r * r * r);
-    } else {
-      const double v = r / hh;
-      const double h3 = 1.0 / (hh * hh * hh);
-      if (v < 0.5) K = h3 * (32.0 / 3.0 + v * v * (32.0 * v - 38.4));
-      else K = h3 * (64.0 / 3.0 - 48.0 * v + 38.4 * v * v - (32.0 / 3.0) * v * v * v - (1.0 / 15.0) / (v * v * v));
-    }
-    const double u = r * A.inv2rs64;
-    const double f = erfc(u) + 1.1283791670955126 * u * exp(-u * u);
-    const double sc = -d[3] * K * f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) a[c] += sc * dv[c];
-    ++nint;
-  }
-
-  __device__ void evaluate(const WalkArgs& A, const WarpBufs& W, Stage& St, Smem&, int nq, int lane,
-                           const GroupInfo&, int64_t, uint32_t, float) {
-    const int total = queue_offsets(A, W, nq, lane);
-    if (total < 0) {
-      if (lane == 0) set_status(A.wsb, ST_TREELINK);
-      return;
-    }
-    for (int base = 0; base < total; base += kSlots) {
-      const int cnt = min(kSlots, total - base);
-      if (lane < cnt) stage(A, W, St, nq, total, base + lane, lane);
-      __syncwarp();
-      for (int t = 0; t < cnt; ++t) pair(A, St, t, lane);
-      __syncwarp();
-    }
-  }
-
-  __device__ void finish(const WalkArgs& A) {
-    if (!valid) return;
-    const int32_t i = A.T.order[k];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) A.accd[3 * (int64_t)i + c] = a[c];
-    if (A.counts) A.counts[i] = nint;
-  }
-};
+template <bool ADJ>
+using LaneF32 = LaneFP<ADJ, false>;
+using LaneF64 = LaneFP<false, true>;
 
 // ------------------------------------------------------------------ traversal
 
