@@ -10,10 +10,9 @@
 // parent's range, so the child runs come out without touching every key.
 // Child slots are taken per block with a single atomic on the level counter.
 //
-// Bottom-up moments: one launch per level, deepest first.  Eight lanes serve
-// one node; each lane reduces one child (or a strided share of a leaf's
-// particles) in FP64 and the eight partial sums are combined with shuffles in
-// a fixed order, so the result does not depend on scheduling.
+// Bottom-up moments: one launch per level, deepest first.  One thread serves
+// one node and sums its children (or a leaf's particles) in FP64 in index
+// order, so the result does not depend on scheduling.
 #include "og_internal.cuh"
 
 namespace og {
@@ -155,26 +154,25 @@ __global__ void __launch_bounds__(256) k_expand(TreeDev T, const uint64_t* __res
   }
 }
 
-// Bottom-up moments for one level.  8 lanes per node.
+// Bottom-up moments for one level, one thread per node.  A leaf sums its
+// particles and an internal node its children, in index order; then the
+// node's centre of mass, split FP32 copies and cube centre are written.  On
+// this GPU an FP64 warp instruction costs the same however many lanes are
+// active, so giving each lane its own node (rather than spreading one node
+// over several lanes) minimises FP64 instructions per node.
 __global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, BoxScale B) {
   const int base = level_base(T.sb, lev);
   const int cnt = T.sb->level_cnt[lev];
   if (base + cnt > T.cap) return;  // capacity already exceeded (flagged by k_expand)
-  const int sub = threadIdx.x & 7;
   const double side = ldexp(B.L, -lev);
   const float side_b = ldexpf(1.0f, -lev);
   const double invL = B.invL, invL2 = B.invL * B.invL;
-  // warp-uniform loop bound: the 4 node groups of a warp stay together for the shuffles
-  const int stride = (gridDim.x * blockDim.x) >> 3;
-  for (int wstep = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3; wstep < cnt; wstep += stride) {
-    const int step = wstep + ((threadIdx.x & 31) >> 3);
-    const bool live = step < cnt;
+  for (int step = blockIdx.x * blockDim.x + threadIdx.x; step < cnt; step += gridDim.x * blockDim.x) {
     const int p = base + step;
-    const int4 D = live ? T.nD[p] : make_int4(0, 0, -1, 0);
+    const int4 D = T.nD[p];
     double M = 0.0, S0 = 0.0, S1 = 0.0, S2 = 0.0, H = 0.0;
-    if (!live) {
-    } else if (meta_leaf(D.w)) {
-      for (int j = D.x + sub; j < D.x + D.y; j += 8) {
+    if (meta_leaf(D.w)) {
+      for (int j = D.x; j < D.x + D.y; ++j) {
         const double m = T.m64[j];
         M += m;
         S0 += m * T.x64[3 * (int64_t)j];
@@ -183,50 +181,42 @@ __global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, BoxScale B)
         H = fmax(H, T.h64[j]);
         T.leaf_of[j] = p;
       }
-    } else if (sub < meta_nchild(D.w)) {
-      const int c = D.z + sub;
-      M = T.mass64[c];
-      S0 = T.S64[3 * (int64_t)c];
-      S1 = T.S64[3 * (int64_t)c + 1];
-      S2 = T.S64[3 * (int64_t)c + 2];
-      H = T.hmax64[c];
+    } else {
+      const int c1 = D.z + meta_nchild(D.w);
+      for (int c = D.z; c < c1; ++c) {
+        M += T.mass64[c];
+        S0 += T.S64[3 * (int64_t)c];
+        S1 += T.S64[3 * (int64_t)c + 1];
+        S2 += T.S64[3 * (int64_t)c + 2];
+        H = fmax(H, T.hmax64[c]);
+      }
     }
+    const double invM = 1.0 / M;
+    const double com[3] = {S0 * invM, S1 * invM, S2 * invM};
+    float hi[3], lo[3];
+    double cen[3];
+    float cenb[3];
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      M += __shfl_xor_sync(0xffffffffu, M, o, 8);
-      S0 += __shfl_xor_sync(0xffffffffu, S0, o, 8);
-      S1 += __shfl_xor_sync(0xffffffffu, S1, o, 8);
-      S2 += __shfl_xor_sync(0xffffffffu, S2, o, 8);
-      H = fmax(H, __shfl_xor_sync(0xffffffffu, H, o, 8));
-    }
-    // Finalisation, spread over the node's lanes: lane 0 writes the sums,
-    // mass and softening; lanes 1-3 each take one coordinate.  FP64 work
-    // costs one warp instruction however many lanes are active, so the
-    // three coordinates cost what one does.
-    if (live && sub == 0) {
-      const double hb = H * invL;
-      T.mass64[p] = M;
-      T.hmax64[p] = H;
-      T.S64[3 * (int64_t)p] = S0;
-      T.S64[3 * (int64_t)p + 1] = S1;
-      T.S64[3 * (int64_t)p + 2] = S2;
-      reinterpret_cast<float*>(&T.nA[p])[3] = (float)(M * invL2);
-      reinterpret_cast<float*>(&T.nB[p])[3] = (float)(hb * hb);
-      reinterpret_cast<float*>(&T.nC[p])[3] = side_b;
-    }
-    if (live && sub >= 1 && sub <= 3) {
-      const int c = sub - 1;
-      const double Sc = c == 0 ? S0 : (c == 1 ? S1 : S2);
-      const double com = Sc * (1.0 / M);
-      float hi, lo;
-      split_coord(com * invL, hi, lo);
+    for (int c = 0; c < 3; ++c) {
+      split_coord(com[c] * invL, hi[c], lo[c]);
       const uint32_t q = quantise(T.x64[3 * (int64_t)D.x + c], B) >> (kMaxLevel - lev);
-      T.com64[3 * (int64_t)p + c] = com;
-      T.cen64[3 * (int64_t)p + c] = __dmul_rn((double)q + 0.5, side);
-      reinterpret_cast<float*>(&T.nA[p])[c] = hi;
-      reinterpret_cast<float*>(&T.nB[p])[c] = lo;
-      reinterpret_cast<float*>(&T.nC[p])[c] = ((float)q + 0.5f) * side_b;
+      cen[c] = __dmul_rn((double)q + 0.5, side);
+      cenb[c] = ((float)q + 0.5f) * side_b;
     }
+    const double hb = H * invL;
+    T.mass64[p] = M;
+    T.hmax64[p] = H;
+    T.S64[3 * (int64_t)p] = S0;
+    T.S64[3 * (int64_t)p + 1] = S1;
+    T.S64[3 * (int64_t)p + 2] = S2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T.com64[3 * (int64_t)p + c] = com[c];
+      T.cen64[3 * (int64_t)p + c] = cen[c];
+    }
+    T.nA[p] = make_float4(hi[0], hi[1], hi[2], (float)(M * invL2));
+    T.nB[p] = make_float4(lo[0], lo[1], lo[2], (float)(hb * hb));
+    T.nC[p] = make_float4(cenb[0], cenb[1], cenb[2], side_b);
   }
 }
 
