@@ -4,21 +4,25 @@
 // (lane = target).  The warp keeps a stack of (first node, node count, lane
 // mask) ranges in shared memory and pops up to 32 nodes per step, one per
 // lane.  Each node is first classified against the bounding box of the whole
-// group (drop / open / accept / mixed); only mixed nodes take per-lane
-// decisions.  Opened internal nodes push their children as one range with the
-// mask of the lanes that opened them; opened leaves and accepted nodes are
-// queued.  Each target therefore receives exactly the terms of its own
-// per-particle walk (the rules are listed in og.h), while node data is read
-// once per warp.
+// group (drop / open / accept / mixed); a mixed node is classified again
+// against the boxes of the four 8-target sub-groups, and only the sub-groups
+// left undecided take per-lane decisions.  Opened internal nodes push their
+// children as one range with the mask of the lanes that opened them; opened
+// leaves and accepted nodes are queued.  Each target therefore receives
+// exactly the terms of its own per-particle walk (the rules are listed in
+// og.h), while node data is read once per warp.
 //
-// Evaluation (FP32).  Queued entries are expanded into source slots and
-// staged in shared memory 32 at a time.  A cheap conservative test (|x_i|^2 +
-// |x_j|^2 - 2 x_i.x_j against r_cut^2, with a per-slot rounding margin) marks
-// the (target, source) pairs that can lie inside the cut; the marked pairs are
-// compacted into a target-major list by a warp prefix sum, and each warp
-// iteration evaluates 32 listed pairs.  Every target then sums its own pair
-// results in slot order, so the result does not depend on which lane
-// evaluated a pair.  The FP64 variant evaluates the staged slots in lockstep.
+// Evaluation.  Queued entries are expanded into source slots; a source
+// beyond r_cut of the group box is dropped and the others are staged in a
+// ring of two 32-slot batches.  For a batch, a cheap conservative test
+// (|x_i|^2 + |x_j|^2 - 2 x_i.x_j against r_cut^2, with a per-slot rounding
+// margin) marks the (target, source) pairs that can lie inside the cut; the
+// marked pairs are compacted into a target-major list by a warp prefix sum,
+// and each warp iteration evaluates 32 listed pairs.  A segmented scan over
+// the lanes sums each target's run in a fixed order, so the result does not
+// depend on scheduling.  The adjoint sums each source's terms over the lanes
+// holding it (match_any groups, lane order).  The FP64 variant shares all of
+// this with FP64 decisions and pair arithmetic.
 //
 // FP32 path.  Positions are split floats in box units (hi a multiple of 2^-23,
 // lo the rest), so hi_i - hi_j is exact and every displacement
@@ -160,12 +164,6 @@ __device__ __forceinline__ void kahan_add(float& T, float& C, float x) {
   const float t = T + y;
   C = (t - T) - y;
   T = t;
-}
-
-__device__ __forceinline__ float warp_sum(float v, uint32_t m = 0xffffffffu) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o);
-  return v;
 }
 
 // Exact float -> double by bit manipulation on the integer pipe (the FP64
