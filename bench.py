@@ -276,15 +276,27 @@ def main():
 
     state = {}
 
+    def part_keys():
+        state["ko"] = og.keys_sort(pos, w.box, check=False, ws=ws_keys, keys=keys, order=order)
+
+    def part_tree():
+        k, o = state["ko"]
+        state["tree"] = og.tree_build(k, o, pos, mass, eps, w.box, p=p, check=False, mem=tree_mem)
+
+    def part_accel():
+        og.shortrange_accel(state["tree"], w.r_s, args.theta, check=False, ws=ws_acc, out=acc, total=total)
+
+    def part_adjoint():
+        og.shortrange_adjoint(state["tree"], w.r_s, args.theta, wt, check=False, ws=ws_adj, dpos=dpos, dmass=dmass)
+
     def step(ev=None):
-        k, o = og.keys_sort(pos, w.box, check=False, ws=ws_keys, keys=keys, order=order)
+        part_keys()
         if ev: ev[1].record()
-        tr = og.tree_build(k, o, pos, mass, eps, w.box, p=p, check=False, mem=tree_mem)
+        part_tree()
         if ev: ev[2].record()
-        og.shortrange_accel(tr, w.r_s, args.theta, check=False, ws=ws_acc, out=acc, total=total)
+        part_accel()
         if ev: ev[3].record()
-        og.shortrange_adjoint(tr, w.r_s, args.theta, wt, check=False, ws=ws_adj, dpos=dpos, dmass=dmass)
-        state["tree"] = tr
+        part_adjoint()
 
     for _ in range(args.warmup):
         step()
@@ -293,11 +305,24 @@ def main():
     # are fixed (per-level sizes live on the device), so a whole step can be
     # captured once and replayed as one CUDA graph.
     graph = None
+    parts = None
     if not args.no_graph:
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
             step()
         graph.replay()
+        torch.cuda.synchronize()
+        # the same step as three graphs, for the end-to-end run (host copies
+        # overlap the parts that do not need them)
+        parts = []
+        for fns in ((part_keys,), (part_tree, part_accel), (part_adjoint,)):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                for f in fns:
+                    f()
+            parts.append(g)
+        for g in parts:
+            g.replay()
         torch.cuda.synchronize()
 
     def run_step(ev=None):
@@ -378,15 +403,46 @@ def main():
     h2d = pos_h.numel() * 8 + mass_h.numel() * 8 + eps_h.numel() * 8 + wt_h.numel() * 4
     d2h = acc_h.numel() * 4 + dpos_h.numel() * 8 + dmass_h.numel() * 8
 
+    # End to end: the positions go up first (keys need them); masses,
+    # softenings and loss weights go up on a copy stream while keys and sort
+    # run; the accelerations come back while the adjoint runs.  The copy
+    # stream starts after the step's start event and is joined before its end.
+    cstream = torch.cuda.Stream(device=dev)
+    ev_go = torch.cuda.Event()
+    ev_me = torch.cuda.Event()
+    ev_wt = torch.cuda.Event()
+    ev_acc = torch.cuda.Event()
+
+    def run_part(i, fns):
+        if parts is not None:
+            parts[i].replay()
+        else:
+            for f in fns:
+                f()
+
     def e2e_step():
+        main = torch.cuda.current_stream()
+        ev_go.record(main)
         pos.copy_(pos_h, non_blocking=True)
-        mass.copy_(mass_h, non_blocking=True)
-        eps.copy_(eps_h, non_blocking=True)
-        wt.copy_(wt_h, non_blocking=True)
-        run_step()
-        acc_h.copy_(acc, non_blocking=True)
+        with torch.cuda.stream(cstream):
+            cstream.wait_event(ev_go)
+            mass.copy_(mass_h, non_blocking=True)
+            eps.copy_(eps_h, non_blocking=True)
+            ev_me.record(cstream)
+            wt.copy_(wt_h, non_blocking=True)
+            ev_wt.record(cstream)
+        run_part(0, (part_keys,))
+        main.wait_event(ev_me)
+        run_part(1, (part_tree, part_accel))
+        ev_acc.record(main)
+        with torch.cuda.stream(cstream):
+            cstream.wait_event(ev_acc)
+            acc_h.copy_(acc, non_blocking=True)
+        main.wait_event(ev_wt)
+        run_part(2, (part_adjoint,))
         dpos_h.copy_(dpos, non_blocking=True)
         dmass_h.copy_(dmass, non_blocking=True)
+        main.wait_stream(cstream)
 
     e2e_step()
     torch.cuda.synchronize()
