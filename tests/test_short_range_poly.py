@@ -58,7 +58,13 @@ def test_table_is_what_the_generator_writes():
     spec = importlib.util.spec_from_file_location(
         "fit_short_range_poly", os.path.join(ROOT, "paper_2606_17145_gb300", "csrc", "fit_short_range_poly.py"))
     mod = importlib.util.module_from_spec(spec)
-    spec.loader.exec_module(mod)
+    import sys
+    keep = sys.dont_write_bytecode
+    sys.dont_write_bytecode = True  # no cache files next to the CUDA sources
+    try:
+        spec.loader.exec_module(mod)
+    finally:
+        sys.dont_write_bytecode = keep
     coeffs, err = mod.fit()
     assert np.array_equal(np.asarray(coeffs, dtype=np.float64).astype(np.float32), _coefficients())
     assert err <= 2.5e-7
