@@ -237,16 +237,16 @@ def main():
 
     import torch
     import __graft_entry__
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)  # before any collective: each rank on its own GPU
     if rank == 0 or ws == 1:
         __graft_entry__.build()
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-        dist.barrier()
+        dist.init_process_group("nccl", device_id=dev)
+        dist.barrier(device_ids=[local])
         __graft_entry__.build()
     import paper_2606_17145_gb300 as og
-    dev = torch.device(f"cuda:{local}")
-    torch.cuda.set_device(dev)
     L = og.lib()
 
     # resident inputs, preallocated outputs and workspaces (no allocation in the timed region)
@@ -340,7 +340,7 @@ def main():
     per = {k: [] for k in phases}
     step_ms = []
     if ws > 1:
-        torch.distributed.barrier()
+        torch.distributed.barrier(device_ids=[local])
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         t_wall = time.time()
@@ -505,7 +505,7 @@ def main():
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                                 "particles_per_s": pps}
     if ws > 1:
-        torch.distributed.barrier()
+        torch.distributed.barrier(device_ids=[local])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
