@@ -77,3 +77,15 @@ def test_nonfinite_positions_flagged():
     with pytest.raises(m.OGError) as e:
         m.keys_sort(pos, 1.0)
     assert e.value.code == 1
+
+
+def test_non_power_of_two_box_with_wrap(orc):
+    """A box side that is not a power of two takes the IEEE division in the
+    wrap and the quantisation; positions span several periods."""
+    rng = np.random.default_rng(91)
+    L = 3.0
+    pos = rng.random((50000, 3)) * 5.0 * L - 2.0 * L
+    # and points just around quantisation boundaries of that box
+    q = rng.integers(0, 1 << 21, size=(5000, 3)).astype(np.float64)
+    edge = np.concatenate([q * (L / (1 << 21)), np.nextafter(q * (L / (1 << 21)), -np.inf)])
+    _check(np.concatenate([pos, edge]), orc, box=L)

@@ -219,3 +219,74 @@ def test_single_range_pops_adjoint(orc):
     op, om = _oracle_tree(orc, w).adjoint(w.r_s, w.rcut, 0.5, wt, s)
     assert np.abs(gp[s] - op).max() / np.abs(op).max() < 2e-5
     assert np.abs(gm[s] - om).max() / np.abs(om).max() < 2e-5
+
+
+def _scaled(w, L):
+    w.pos = w.pos * L
+    w.box = L
+    w.r_s = w.r_s * L
+    w.eps = w.eps * L
+    return w
+
+
+def test_non_power_of_two_box_vs_tree(orc):
+    """Box side 3 (not a power of two): the tree build divides by L."""
+    dev = device()
+    w = _scaled(ics.make("nfw256", 20), 3.0)
+    a, tot, cnt, _ = forward(w, dev, 0.5)
+    ao, co = orc.Tree(w.pos, w.mass, 2.8 * w.eps, box=3.0).walk(w.r_s, w.rcut, 0.5)
+    assert np.array_equal(cnt, co)
+    assert err_stats(a, ao)["rms"] <= 1e-5
+
+
+def test_non_power_of_two_box_adjoint(orc):
+    dev = device()
+    m = og()
+    w = _scaled(ics.make("nfw256", 16), 3.0)
+    wt = ics.loss_weights(w.n, 12).astype(np.float32).astype(np.float64)
+    from gpu_util import build_tree
+    tree, _, _ = build_tree(w, dev)
+    dpos, dmass = m.shortrange_adjoint(tree, w.r_s, 0.5, torch.tensor(wt, dtype=torch.float32, device=dev))
+    gp, gm = dpos.cpu().numpy(), dmass.cpu().numpy()
+    s = np.arange(0, w.n, 7)
+    op, om = orc.Tree(w.pos, w.mass, 2.8 * w.eps, box=3.0).adjoint(w.r_s, w.rcut, 0.5, wt, s)
+    assert np.abs(gp[s] - op).max() / np.abs(op).max() < 2e-5
+    assert np.abs(gm[s] - om).max() / np.abs(om).max() < 2e-5
+
+
+def test_momentum_at_theta_zero():
+    """At theta = 0 every term is a particle pair, and pair forces are
+    antisymmetric: sum_i m_i a_i vanishes up to FP32 rounding of the terms."""
+    dev = device()
+    w = ics.make("zeldovich128", 27)   # 19,683 particles
+    a, tot, cnt, _ = forward(w, dev, 0.0)
+    ma = w.mass[:, None] * a
+    assert np.abs(ma.sum(axis=0)).max() <= 1e-5 * np.abs(ma).sum(axis=0).max()
+
+
+def test_large_opening_angle_vs_tree(orc):
+    """theta = 1.2: far more accepted nodes and mixed decisions."""
+    dev = device()
+    w = ics.make("nfw256", 24)
+    a, tot, cnt, _ = forward(w, dev, 1.2)
+    ao, co = _oracle_tree(orc, w).walk(w.r_s, w.rcut, 1.2)
+    assert np.array_equal(cnt, co)
+    assert err_stats(a, ao)["rms"] <= 1e-5
+
+
+def test_coincident_particles(orc):
+    """100 particles at one point (a level-21 leaf that cannot split) in a
+    background: their mutual pairs count and give zero force, nothing is NaN."""
+    dev = device()
+    rng = np.random.default_rng(93)
+    pos = np.concatenate([np.full((100, 3), 0.3141592653589793), rng.random((1900, 3))])
+    n = pos.shape[0]
+    w = ics.Workload("coincident", pos, np.full(n, 1.0 / n), np.full(n, 1e-3), 1.0, 0.02, (0.5,))
+    a, tot, cnt, _ = forward(w, dev, 0.5)
+    ao, co = _oracle_tree(orc, w).walk(w.r_s, w.rcut, 0.5)
+    assert np.all(np.isfinite(a))
+    assert np.array_equal(cnt, co)
+    assert cnt[:100].min() >= 99
+    assert err_stats(a[100:], ao[100:])["rms"] <= 1e-5
+    # the coincident ones feel only the background
+    assert np.abs(a[:100] - ao[:100]).max() <= 1e-5 * np.abs(ao[:100]).max() + 1e-12
