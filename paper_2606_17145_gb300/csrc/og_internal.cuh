@@ -209,12 +209,13 @@ __device__ inline void split_coord(double xi, float& hi, float& lo) {
 struct BoxScale {
   double L, invL;
   int pow2;
+  int e;  // L = 2^e when pow2
 };
 
 inline BoxScale box_scale(double L) {
   int e = 0;
-  const double m = std::frexp(L, &e);
-  return BoxScale{L, 1.0 / L, m == 0.5 ? 1 : 0};
+  const double m = std::frexp(L, &e);  // L = m 2^e, m in [0.5, 1)
+  return BoxScale{L, 1.0 / L, m == 0.5 ? 1 : 0, e - 1};
 }
 
 __device__ inline double div_box(double x, const BoxScale& B) {
@@ -225,14 +226,29 @@ __device__ inline double div_box(double x, const BoxScale& B) {
 // (no fused multiply-add: the result must be bit-identical to the host form).
 __device__ inline double wrap_coord(double x, const BoxScale& B) {
   // power-of-two side and 0 < x < L: x / L is exact and below 1, so the
-  // general form returns x itself
-  if (B.pow2 && x > 0.0 && x < B.L) return x;
+  // general form returns x itself.  Positive doubles order like their bit
+  // patterns, so the range test needs no FP64 compare.
+  const long long xb = __double_as_longlong(x);
+  if (B.pow2 && xb > 0 && xb < __double_as_longlong(B.L)) return x;
   double fl = floor(div_box(x, B));
   double prod = __dmul_rn(B.L, fl);
   return __dsub_rn(x, prod);
 }
 
 __device__ inline uint32_t quantise(double w, const BoxScale& B) {
+  if (B.pow2) {
+    // w (2^21 / L) = w 2^(21 - e) is exact for a power-of-two side, so its
+    // floor is the integer part of the mantissa shifted by the exponent
+    const long long wb = __double_as_longlong(w);
+    if (wb <= 0) return 0u;                       // +-0 (and negatives)
+    const int E = (int)((wb >> 52) & 0x7ff);
+    if (E == 0) return 0u;                        // subnormal: far below one cell
+    const int sh = E - 1023 + 21 - B.e;           // w 2^(21-e) = 1.f 2^sh
+    if (sh < 0) return 0u;
+    if (sh >= 21) return 2097151u;                // w >= L: clamp (w is finite here)
+    const unsigned long long mant = ((unsigned long long)wb & 0x000fffffffffffffull) | 0x0010000000000000ull;
+    return (uint32_t)(mant >> (52 - sh));
+  }
   double t = __dmul_rn(div_box(w, B), 2097152.0);
   double fl = floor(t);
   if (fl < 0.0) return 0u;

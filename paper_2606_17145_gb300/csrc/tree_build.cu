@@ -47,18 +47,28 @@ __global__ void k_permute(BuildArgs A, BoxScale B) {
 }
 
 __global__ void k_groups(TreeDev T, BoxScale B) {
+  // Wrapped positions are non-negative doubles, which order like their bit
+  // patterns, and division by L is monotonic: the box in box units is the
+  // division of the integer min / max.
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < T.ngroups; g += (int64_t)gridDim.x * blockDim.x) {
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    long long lo[3] = {0x7fffffffffffffffll, 0x7fffffffffffffffll, 0x7fffffffffffffffll};
+    long long hi[3] = {0, 0, 0};
     const int64_t a = g * kGroup, b = (T.n < a + kGroup ? T.n : a + kGroup);
     for (int64_t k = a; k < b; ++k)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double x = div_box(T.x64[3 * k + c], B);
-        lo[c] = fmin(lo[c], x);
-        hi[c] = fmax(hi[c], x);
+        const long long x = __double_as_longlong(T.x64[3 * k + c]);
+        lo[c] = x < lo[c] ? x : lo[c];
+        hi[c] = x > hi[c] ? x : hi[c];
       }
-    T.gbox[2 * g] = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]), __double2float_rd(lo[2]), 0.f);
-    T.gbox[2 * g + 1] = make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]), __double2float_ru(hi[2]), 0.f);
+    float fl[3], fh[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      fl[c] = __double2float_rd(div_box(__longlong_as_double(lo[c]), B));
+      fh[c] = __double2float_ru(div_box(__longlong_as_double(hi[c]), B));
+    }
+    T.gbox[2 * g] = make_float4(fl[0], fl[1], fl[2], 0.f);
+    T.gbox[2 * g + 1] = make_float4(fh[0], fh[1], fh[2], 0.f);
   }
 }
 
