@@ -20,9 +20,10 @@
 // marked pairs are compacted into a target-major list by a warp prefix sum,
 // and each warp iteration evaluates 32 listed pairs.  A segmented scan over
 // the lanes sums each target's run in a fixed order, so the result does not
-// depend on scheduling.  The adjoint sums each source's terms over the lanes
-// holding it (match_any groups, lane order).  The FP64 variant shares all of
-// this with FP64 decisions and pair arithmetic.
+// depend on scheduling.  In the adjoint, the lane that owns a slot sums that
+// source's terms over the iteration's lanes in lane order (their lanes are
+// found through a shared-memory bit mask per slot).  The FP64 variant shares
+// all of this with FP64 decisions and pair arithmetic.
 //
 // FP32 path.  Positions are split floats in box units (hi a multiple of 2^-23,
 // lo the rest), so hi_i - hi_j is exact and every displacement
@@ -429,7 +430,8 @@ struct LaneFP {
     float4 tA[kGroup];    // targets: hi part, h^2
     float4 tB[kGroup];    // targets: lo part
     float4 tW[ADJ ? kGroup : 1];   // adjoint: dL/da of each target
-    float4 GS[ADJ ? kSlots : 1];  // adjoint: each slot's source-side sums (G, S) over the batch
+    float4 SG[ADJ ? kGroup : 1];     // adjoint: source-side term (G, S) of each lane's listed pair
+    uint32_t smask[ADJ ? kSlots : 1];  // adjoint: the lanes whose listed pair has this slot
     int self[kGroup];     // staged slot holding the target itself, or -1
     typename std::conditional<F64, double3, float4>::type Ps[kGroup];  // each target's sum over the batch
     int fneg[kGroup];     // listed pairs of the batch found outside the exact cut
@@ -461,6 +463,7 @@ struct LaneFP {
   float S[3], C[3];   // Kahan total and compensation
   double a64[3];      // FP64 variant: plain double sums
   int nint;
+  float4 gs;          // adjoint: this lane's slot, source-side sums (G, S) over the batch
 
   __device__ void init(const WalkArgs& A, Smem& M, int64_t kk, bool v, int lane, const GroupInfo& G) {
     k = kk;
@@ -474,7 +477,7 @@ struct LaneFP {
     else M.Ps[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     a64[0] = a64[1] = a64[2] = 0.0;
     M.fneg[lane] = 0;
-    if (ADJ) M.GS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ADJ) { gs = make_float4(0.f, 0.f, 0.f, 0.f); M.smask[lane] = 0u; }
     xr[0] = (a.x - G.cx) + b.x;
     xr[1] = (a.y - G.cy) + b.y;
     xr[2] = (a.z - G.cz) + b.z;
@@ -820,34 +823,30 @@ struct LaneFP {
             M.Ps[i] = a;
           }
           if (ADJ) {
-            // source-side terms: the lanes holding the same slot are summed
-            // in lane order onto the lowest of them, which adds the sum to
-            // the slot's batch total (one writer per slot per iteration)
-            const uint32_t grp = __match_any_sync(0xffffffffu, hv ? slot : 32 + lane);
-            const int gmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(grp));
-            uint32_t rest = grp & (grp - 1u);
-            float4 acc = sg;
-            for (int k = 1; k < gmax; ++k) {
-              const int src = rest ? __ffs(rest) - 1 : lane;
-              const float v0 = __shfl_sync(0xffffffffu, sg.x, src);
-              const float v1 = __shfl_sync(0xffffffffu, sg.y, src);
-              const float v2 = __shfl_sync(0xffffffffu, sg.z, src);
-              const float v3 = __shfl_sync(0xffffffffu, sg.w, src);
-              if (rest) {
-                acc.x += v0;
-                acc.y += v1;
-                acc.z += v2;
-                acc.w += v3;
-                rest &= rest - 1u;
+            // source-side terms: each listed pair's term goes to shared
+            // memory with its lane bit in its slot's mask; the lane that owns
+            // the slot sums them in lane order and adds the sum to its batch
+            // total, kept in registers
+            M.SG[lane] = sg;
+            if (hv) atomicOr(&M.smask[slot], 1u << lane);
+            __syncwarp();
+            uint32_t mk = M.smask[lane];
+            if (mk) {
+              M.smask[lane] = 0u;
+              float4 acc = M.SG[__ffs(mk) - 1];
+              mk &= mk - 1u;
+              while (mk) {
+                const float4 v = M.SG[__ffs(mk) - 1];
+                acc.x += v.x;
+                acc.y += v.y;
+                acc.z += v.z;
+                acc.w += v.w;
+                mk &= mk - 1u;
               }
-            }
-            if (hv && lane == __ffs(grp) - 1) {
-              float4 g = M.GS[slot];
-              g.x += acc.x;
-              g.y += acc.y;
-              g.z += acc.z;
-              g.w += acc.w;
-              M.GS[slot] = g;
+              gs.x += acc.x;
+              gs.y += acc.y;
+              gs.z += acc.z;
+              gs.w += acc.w;
             }
           }
           __syncwarp();
@@ -875,7 +874,7 @@ struct LaneFP {
     }
     if constexpr (!F64) fold();
     if (ADJ) {
-      const float4 g = M.GS[lane];
+      const float4 g = gs;
       if (has && (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f)) {
         const int id = St.sc[hb + lane].x;
         double* Gd = id >= 0 ? A.Gp + 3 * (int64_t)id : A.Gn + 3 * (int64_t)(-2 - id);
@@ -885,7 +884,7 @@ struct LaneFP {
         atomicAdd(Gd + 2, f2d_exact(g.z));
         atomicAdd(Sd, f2d_exact(g.w));
       }
-      M.GS[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      gs = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // this batch held the target's own slot
     if (self_here) M.self[lane] = -1;
