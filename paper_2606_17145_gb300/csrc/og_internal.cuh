@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/og.h"
+#include "split_coord.cuh"
 
 namespace og {
 
@@ -195,12 +196,18 @@ inline size_t carve_adj(void* buf, int64_t n, int64_t cap, AdjWs* W) {
 
 __device__ inline void set_status(StatusBlock* sb, uint32_t bits) { atomicOr(&sb->status, bits); }
 
-// Split a box-unit coordinate xi in [0, 1] into (hi, lo): hi = k 2^-23.
-__device__ inline void split_coord(double xi, float& hi, float& lo) {
+// Split a box-unit coordinate xi in [0, 1] into (hi, lo): hi = k 2^-23 with
+// k = rint(xi 2^23), lo = xi - hi rounded to FP32.  This is the definition;
+// split_coord takes the integer form where it applies.
+__device__ inline void split_coord_f64(double xi, float& hi, float& lo) {
   double k = rint(xi * 8388608.0);
   double h = k * (1.0 / 8388608.0);
   hi = static_cast<float>(h);
   lo = static_cast<float>(xi - h);
+}
+
+__device__ inline void split_coord(double xi, float& hi, float& lo) {
+  if (!split_bits((uint64_t)__double_as_longlong(xi), 0, hi, lo)) split_coord_f64(xi, hi, lo);
 }
 
 // Division by the box side.  When L is a power of two, x / L equals
@@ -220,6 +227,13 @@ inline BoxScale box_scale(double L) {
 
 __device__ inline double div_box(double x, const BoxScale& B) {
   return B.pow2 ? __dmul_rn(x, B.invL) : __ddiv_rn(x, B.L);
+}
+
+// (hi, lo) of x / L.  For a power-of-two side, x / L = x 2^-e exactly where
+// it is normal, so the integer split reads the bits of x itself.
+__device__ inline void split_box(double x, const BoxScale& B, float& hi, float& lo) {
+  if (B.pow2 && split_bits((uint64_t)__double_as_longlong(x), B.e, hi, lo)) return;
+  split_coord(div_box(x, B), hi, lo);
 }
 
 // Periodic wrap into [0, L]: x - L floor(x / L), each operation rounded once

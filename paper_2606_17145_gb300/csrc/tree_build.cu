@@ -18,6 +18,16 @@
 namespace og {
 
 
+// Finite: exponent field not all ones.  Positive and finite: the bits, as an
+// unsigned integer, lie in [1, 0x7fefffffffffffff].  (Integer tests: the FP64
+// pipe is the scarce one.)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((uint64_t)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool positive_finite_bits(double x) {
+  return (uint64_t)__double_as_longlong(x) - 1ull < 0x7fefffffffffffffull;
+}
+
 __global__ void k_permute(BuildArgs A, BoxScale B) {
   const TreeDev& T = A.T;
   const double invL2 = B.invL * B.invL;
@@ -25,24 +35,36 @@ __global__ void k_permute(BuildArgs A, BoxScale B) {
     const int32_t i = A.order[k];
     double w[3];
     float hi[3], lo[3];
+    bool ok = true;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      w[c] = wrap_coord(A.pos[3 * (int64_t)i + c], B);
-      split_coord(div_box(w[c], B), hi[c], lo[c]);
+      const double x = A.pos[3 * (int64_t)i + c];
+      ok = ok && finite_bits(x);
+      w[c] = wrap_coord(x, B);
+      split_box(w[c], B, hi[c], lo[c]);
       T.x64[3 * k + c] = w[c];
     }
     const double m = A.mass[i];
     const double eps = A.eps ? A.eps[i] : A.eps_scalar;
-    if (!(isfinite(A.pos[3 * (int64_t)i]) && isfinite(A.pos[3 * (int64_t)i + 1]) &&
-          isfinite(A.pos[3 * (int64_t)i + 2]) && m > 0.0 && isfinite(m) && eps > 0.0 && isfinite(eps)))
-      set_status(T.sb, ST_BADINPUT);
+    if (!(ok && positive_finite_bits(m) && positive_finite_bits(eps))) set_status(T.sb, ST_BADINPUT);
     const double h = 2.8 * eps;
-    const double hb = h * B.invL;
     T.m64[k] = m;
     T.h64[k] = h;
     T.order[k] = i;
-    T.pA[k] = make_float4(hi[0], hi[1], hi[2], (float)(m * invL2));
-    T.pB[k] = make_float4(lo[0], lo[1], lo[2], (float)(hb * hb));
+    // m / L^2 and (h / L)^2 in FP32.  For a power-of-two side with 2^-2e an
+    // exact double (invL2 then equals it), m invL2 = m 2^-2e and
+    // (h invL)^2 = (h h) 2^-2e wherever the FP32 result is normal, and the
+    // rounding to FP32 is done on the integer pipe.
+    const bool sq = B.pow2 && B.e >= -511 && B.e <= 537;
+    float mw, h2;
+    if (!(sq && d2f_scaled((uint64_t)__double_as_longlong(m), 2 * B.e, mw))) mw = (float)(m * invL2);
+    const double hh = h * h;
+    if (!(sq && d2f_scaled((uint64_t)__double_as_longlong(hh), 2 * B.e, h2))) {
+      const double hb = h * B.invL;
+      h2 = (float)(hb * hb);
+    }
+    T.pA[k] = make_float4(hi[0], hi[1], hi[2], mw);
+    T.pB[k] = make_float4(lo[0], lo[1], lo[2], h2);
   }
 }
 
@@ -208,7 +230,8 @@ __global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, BoxScale B)
     float cenb[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      split_coord(com[c] * invL, hi[c], lo[c]);
+      if (!(B.pow2 && split_bits((uint64_t)__double_as_longlong(com[c]), B.e, hi[c], lo[c])))
+        split_coord(com[c] * invL, hi[c], lo[c]);
       const uint32_t q = quantise(T.x64[3 * (int64_t)D.x + c], B) >> (kMaxLevel - lev);
       cen[c] = __dmul_rn((double)q + 0.5, side);
       cenb[c] = ((float)q + 0.5f) * side_b;
