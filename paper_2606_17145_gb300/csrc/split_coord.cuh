@@ -99,3 +99,31 @@ OG_HD bool d2f_scaled(uint64_t b, int s, float& out) {
 }
 
 }  // namespace og
+
+namespace og {
+
+// The double v 2^x for an odd integer 1 <= v < 2^31, built from its bits:
+// exact, like the FP64 product (v / 2) 2^(x + 1) it replaces (the centre of
+// cell q at level l of a box 2^e is (q + 1/2) 2^(e - l) = (2q + 1) 2^(e - l - 1)).
+// Returns false, writing nothing, where the result would not be a normal
+// double.
+OG_HD bool double_odd_scaled(uint32_t v, int x, double& out) {
+  if ((v & 1u) == 0u) return false;
+#if defined(__CUDA_ARCH__)
+  const int nb = 31 - __clz((int)v);  // floor(log2 v)
+#else
+  const int nb = 31 - __builtin_clz(v);
+#endif
+  const int E = nb + x + 1023;
+  if (E < 1 || E > 2046) return false;
+  const uint64_t man = ((uint64_t)v << (52 - nb)) & 0x000fffffffffffffull;
+  const uint64_t b = ((uint64_t)E << 52) | man;
+#if defined(__CUDA_ARCH__)
+  out = __longlong_as_double((long long)b);
+#else
+  std::memcpy(&out, &b, sizeof out);
+#endif
+  return true;
+}
+
+}  // namespace og

@@ -202,7 +202,10 @@ __global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, BoxScale B)
   for (int step = blockIdx.x * blockDim.x + threadIdx.x; step < cnt; step += gridDim.x * blockDim.x) {
     const int p = base + step;
     const int4 D = T.nD[p];
-    double M = 0.0, S0 = 0.0, S1 = 0.0, S2 = 0.0, H = 0.0;
+    double M = 0.0, S0 = 0.0, S1 = 0.0, S2 = 0.0;
+    // hmax as an integer max of the bit patterns: softenings are positive
+    // (checked by k_permute), and positive doubles order like their bits
+    long long Hb = 0;
     if (meta_leaf(D.w)) {
       for (int j = D.x; j < D.x + D.y; ++j) {
         const double m = T.m64[j];
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, BoxScale B)
         S0 += m * T.x64[3 * (int64_t)j];
         S1 += m * T.x64[3 * (int64_t)j + 1];
         S2 += m * T.x64[3 * (int64_t)j + 2];
-        H = fmax(H, T.h64[j]);
+        Hb = max(Hb, __double_as_longlong(T.h64[j]));
         T.leaf_of[j] = p;
       }
     } else {
@@ -220,9 +223,10 @@ __global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, BoxScale B)
         S0 += T.S64[3 * (int64_t)c];
         S1 += T.S64[3 * (int64_t)c + 1];
         S2 += T.S64[3 * (int64_t)c + 2];
-        H = fmax(H, T.hmax64[c]);
+        Hb = max(Hb, __double_as_longlong(T.hmax64[c]));
       }
     }
+    const double H = __longlong_as_double(Hb);
     const double invM = 1.0 / M;
     const double com[3] = {S0 * invM, S1 * invM, S2 * invM};
     float hi[3], lo[3];
@@ -233,10 +237,19 @@ __global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, BoxScale B)
       if (!(B.pow2 && split_bits((uint64_t)__double_as_longlong(com[c]), B.e, hi[c], lo[c])))
         split_coord(com[c] * invL, hi[c], lo[c]);
       const uint32_t q = quantise(T.x64[3 * (int64_t)D.x + c], B) >> (kMaxLevel - lev);
-      cen[c] = __dmul_rn((double)q + 0.5, side);
+      // (q + 1/2) side, exact for a power-of-two box: (2q + 1) 2^(e - lev - 1)
+      if (!(B.pow2 && double_odd_scaled(2u * q + 1u, B.e - lev - 1, cen[c]))) cen[c] = __dmul_rn((double)q + 0.5, side);
       cenb[c] = ((float)q + 0.5f) * side_b;
     }
-    const double hb = H * invL;
+    // M / L^2 and (hmax / L)^2 in FP32, as in k_permute
+    const bool sq = B.pow2 && B.e >= -511 && B.e <= 537;
+    float mw, h2;
+    if (!(sq && d2f_scaled((uint64_t)__double_as_longlong(M), 2 * B.e, mw))) mw = (float)(M * invL2);
+    const double HH = H * H;
+    if (!(sq && d2f_scaled((uint64_t)__double_as_longlong(HH), 2 * B.e, h2))) {
+      const double hb = H * invL;
+      h2 = (float)(hb * hb);
+    }
     T.mass64[p] = M;
     T.hmax64[p] = H;
     T.S64[3 * (int64_t)p] = S0;
@@ -247,8 +260,8 @@ __global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, BoxScale B)
       T.com64[3 * (int64_t)p + c] = com[c];
       T.cen64[3 * (int64_t)p + c] = cen[c];
     }
-    T.nA[p] = make_float4(hi[0], hi[1], hi[2], (float)(M * invL2));
-    T.nB[p] = make_float4(lo[0], lo[1], lo[2], (float)(hb * hb));
+    T.nA[p] = make_float4(hi[0], hi[1], hi[2], mw);
+    T.nB[p] = make_float4(lo[0], lo[1], lo[2], h2);
     T.nC[p] = make_float4(cenb[0], cenb[1], cenb[2], side_b);
   }
 }

@@ -1,11 +1,12 @@
 """Integer-pipe roundings of the tree build (csrc/split_coord.cuh) on the CPU.
 
 The kernels store positions as split floats (hi = rint(xi 2^23) 2^-23,
-lo = xi - hi rounded to FP32) and masses and softenings as FP32 copies of
-FP64 products with 2^-2e.  split_coord.cuh computes both from the bit
-patterns on the integer pipe; this test compiles that header with g++ and
-holds it, bit for bit, against the FP64 expressions written out in numpy,
-over random values and the rounding edges (ties, powers of two, range ends).
+lo = xi - hi rounded to FP32), masses and softenings as FP32 copies of FP64
+products with 2^-2e, and cube centres (q + 1/2) 2^(e - l) in FP64.
+split_coord.cuh computes these from bit patterns on the integer pipe; this
+test compiles that header with g++ and holds it, bit for bit, against the
+FP64 expressions written out in numpy, over random values and the rounding
+edges (ties, powers of two, range ends).
 """
 import ctypes
 import os
@@ -27,6 +28,9 @@ extern "C" void t_split(const double* x, long n, int s, float* hi, float* lo, in
     std::memcpy(&b, &x[i], 8);
     ok[i] = og::split_bits(b, s, hi[i], lo[i]) ? 1 : 0;
   }
+}
+extern "C" void t_odd(const unsigned* v, const int* x, long n, double* out, int* ok) {
+  for (long i = 0; i < n; ++i) ok[i] = og::double_odd_scaled(v[i], x[i], out[i]) ? 1 : 0;
 }
 extern "C" void t_d2f(const double* x, long n, int s, float* out, int* ok) {
   for (long i = 0; i < n; ++i) {
@@ -52,6 +56,7 @@ def lib(tmp_path_factory):
     P = ctypes.c_void_p
     L.t_split.argtypes = [P, ctypes.c_long, ctypes.c_int, P, P, P]
     L.t_d2f.argtypes = [P, ctypes.c_long, ctypes.c_int, P, P]
+    L.t_odd.argtypes = [P, P, ctypes.c_long, P, P]
     return L
 
 
@@ -153,3 +158,28 @@ def test_d2f_matches_fp64_conversion(lib, s):
     assert not np.any(ok & ~applies)
     assert np.all(ok[applies & (v <= fmax)])
     np.testing.assert_array_equal(_bits(out[ok]), _bits(expect[ok]))
+
+
+def test_odd_scaled_is_the_exact_cell_centre(lib):
+    rng = np.random.default_rng(17)
+    lev = rng.integers(0, 22, 100000)
+    q = (rng.random(100000) * (2.0 ** lev)).astype(np.int64)
+    e = rng.integers(-40, 40, 100000)
+    v = (2 * q + 1).astype(np.uint32)
+    x = (e - lev - 1).astype(np.int32)
+    # range ends: largest and smallest normal results, and just beyond them
+    v = np.concatenate([v, np.array([1, 1, 1, 1, (1 << 22) - 1, (1 << 22) - 1, 3, 2], np.uint32)])
+    x = np.concatenate([x, np.array([-1022, -1023, 1023, 1024, 1023 - 21, 1024 - 21, -1050, 0], np.int32)])
+    out = np.zeros(v.shape, np.float64)
+    ok = np.zeros(v.shape, np.int32)
+    lib.t_odd(_ptr(v), _ptr(x), v.size, _ptr(out), _ptr(ok))
+    ok = ok.astype(bool)
+    with np.errstate(over="ignore"):
+        expect = np.ldexp(v.astype(np.float64), x)  # exact where normal
+    normal = np.isfinite(expect) & (expect >= np.finfo(np.float64).tiny) & (v % 2 == 1)
+    np.testing.assert_array_equal(ok, normal)
+    np.testing.assert_array_equal(out[ok].view(np.uint64), expect[ok].view(np.uint64))
+    # the centre form used by the tree: (q + 1/2) 2^(e - lev)
+    m = ok[:100000]
+    centre = (q[m] + 0.5) * np.ldexp(1.0, e[m] - lev[m])
+    np.testing.assert_array_equal(out[:100000][m], centre)
