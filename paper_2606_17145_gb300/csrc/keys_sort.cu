@@ -70,7 +70,7 @@ __global__ void k_keys(const double* __restrict__ pos, int64_t n, BoxScale B, ui
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double x0 = pos[3 * i], x1 = pos[3 * i + 1], x2 = pos[3 * i + 2];
     uint64_t key = 0;
-    if (isfinite(x0) && isfinite(x1) && isfinite(x2)) {
+    if (finite_bits(x0) && finite_bits(x1) && finite_bits(x2)) {
       const uint32_t q0 = quantise(wrap_coord(x0, B), B);
       const uint32_t q1 = quantise(wrap_coord(x1, B), B);
       const uint32_t q2 = quantise(wrap_coord(x2, B), B);

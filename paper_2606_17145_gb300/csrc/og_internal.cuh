@@ -196,6 +196,16 @@ inline size_t carve_adj(void* buf, int64_t n, int64_t cap, AdjWs* W) {
 
 __device__ inline void set_status(StatusBlock* sb, uint32_t bits) { atomicOr(&sb->status, bits); }
 
+// Finite: exponent field not all ones.  Positive and finite: the bits, as an
+// unsigned integer, lie in [1, 0x7fefffffffffffff].  (Integer tests: the FP64
+// pipe is the scarce one.)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((uint64_t)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool positive_finite_bits(double x) {
+  return (uint64_t)__double_as_longlong(x) - 1ull < 0x7fefffffffffffffull;
+}
+
 // Split a box-unit coordinate xi in [0, 1] into (hi, lo): hi = k 2^-23 with
 // k = rint(xi 2^23), lo = xi - hi rounded to FP32.  This is the definition;
 // split_coord takes the integer form where it applies.

@@ -18,16 +18,6 @@
 namespace og {
 
 
-// Finite: exponent field not all ones.  Positive and finite: the bits, as an
-// unsigned integer, lie in [1, 0x7fefffffffffffff].  (Integer tests: the FP64
-// pipe is the scarce one.)
-__device__ __forceinline__ bool finite_bits(double x) {
-  return ((uint64_t)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
-}
-__device__ __forceinline__ bool positive_finite_bits(double x) {
-  return (uint64_t)__double_as_longlong(x) - 1ull < 0x7fefffffffffffffull;
-}
-
 __global__ void k_permute(BuildArgs A, BoxScale B) {
   const TreeDev& T = A.T;
   const double invL2 = B.invL * B.invL;
