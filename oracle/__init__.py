@@ -5,6 +5,9 @@ path is compared against.  Only the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline / reference leg import this package.  The product
 path never calls it and has no CPU fallback.
 
+The PM long-range complement has its own numpy FP64 oracle in ``og_pm.py``
+(``from oracle import og_pm``).
+
 ``build()`` compiles the C file with gcc (``-O2 -ffp-contract=off``: no fused
 multiply-add, so every FP64 decision formula is evaluated exactly as written).
 """
