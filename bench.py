@@ -477,6 +477,29 @@ def main():
     per_step_launches = (launches["keys_sort"] + launches["tree_build"] + launches["accel"] +
                          launches["adjoint"])
 
+    # the PM long-range complement on the same particles: a separate measurement,
+    # not part of the step above (mesh of 1.25 box / r_s cells per side, so that
+    # r_s is 1.25 mesh cells)
+    pm_n = int(round(1.25 * w.box / w.r_s))
+    plan = og.PMPlan(pm_n)
+    ws_pm = og._workspace(plan.ws_bytes, dev)
+    acc_pm = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    og.pm_accel(plan, pos, mass, w.box, w.r_s, ws=ws_pm, out=acc_pm)  # checked once
+    for _ in range(args.warmup):
+        og.pm_accel(plan, pos, mass, w.box, w.r_s, check=False, ws=ws_pm, out=acc_pm)
+    pm_times = []
+    for _ in range(max(1, min(args.steps, 20))):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        og.pm_accel(plan, pos, mass, w.box, w.r_s, check=False, ws=ws_pm, out=acc_pm)
+        e1.record()
+        torch.cuda.synchronize()
+        pm_times.append(e0.elapsed_time(e1))
+    pm_ms = max_over_ranks(sum(pm_times) / len(pm_times), ws, dev)
+    plan.close()
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -499,6 +522,9 @@ def main():
                  "same_interactions": inter64 == interactions,
                  "fp32_speedup": f64_ms / pms["accel_fp32"], "fp32_vs_fp64": fp32_vs_fp64},
         "wall_s": wall,
+        "pm": {"ngrid": pm_n, "ms": pm_ms, "particles_per_s": ws * n / (pm_ms * 1e-3),
+               "what": "og_pm_accel: CIC deposit, cuFFT R2C, Green's function, cuFFT C2R, "
+                       "difference + interpolation; FP32 mesh; timed apart from the step, L2 flushed"},
     }
     if rank == 0 and not args.no_cpu_baseline:
         v, pps, sample, done, spent = oracle_throughput(w, args.theta)

@@ -10,6 +10,7 @@
  *   og_tree_build         octree with monopole moments, level by level
  *   og_shortrange_accel   warp-coherent Barnes-Hut walk (FP32 + Kahan, or FP64)
  *   og_shortrange_adjoint gradient of L = sum_i w_i . a_i with frozen decisions
+ *   og_pm_accel           the long-range complement on a particle mesh
  *
  * Physics conventions (G = 1, attractive, code units):
  *   a_i = -sum_s m_s K_h(r) f(r) d,  d = x_i - x_s (periodic minimum image),
@@ -228,6 +229,55 @@ og_status og_shortrange_adjoint(const og_tree* t, double r_s, double theta, og_p
  */
 og_status og_keys_sort_noalloc(const double* pos, int64_t n, double box, uint64_t* keys_sorted, int32_t* order,
                                og_stream stream);
+
+/*
+ * PM long-range complement of the TreePM split.
+ *
+ * The paper (Sec. 3.1) adds long-range forces from a particle mesh, which it
+ * solves with FFTW on the host.  Here the mesh is on the device:
+ *   CIC deposit onto N^3 nodes at x = i L / N (periodic);
+ *   FP32 FFT (cuFFT);
+ *   phi_hat = -4 pi rho_hat exp(-k^2 r_s^2) / (k^2 S), with S = prod_a
+ *     sinc^4(kappa_a / N) deconvolving the CIC window twice and phi_hat(0) = 0;
+ *   inverse FFT;
+ *   a four-point central-difference gradient;
+ *   CIC interpolation back to the particles.
+ * G = 1.  With the same r_s, the short-range walk plus this long-range
+ * acceleration is the full periodic force (up to the mesh's discretisation
+ * error and the walk's cut at rcut).
+ *
+ * og_pm_plan_create -- make the cuFFT plans for an N^3 mesh (8 <= ngrid <=
+ *   1024; a power of two is fastest).  The plan is host memory plus cuFFT's
+ *   own tables, which cuFFT allocates on the current device when the plan is
+ *   made (the one place this library lets a callee allocate device memory;
+ *   the work area and the meshes are the caller's workspace).  *plan is NULL
+ *   on error.  Returns OG_EINVAL for a bad ngrid, OG_ECUDA if cuFFT fails.
+ * og_pm_plan_destroy -- release a plan (NULL is ignored).  Not while a call
+ *   that uses it may still run on the GPU.
+ * og_pm_ws_bytes -- workspace bytes for og_pm_accel with this plan: status
+ *   block, real mesh (4 N^3 B), complex mesh (8 N^2 (N/2 + 1) B), cuFFT work
+ *   area.  0 for a NULL plan.
+ * og_pm_accel -- long-range accelerations.
+ *   pos   device double[n][3], any real values (wrapped into [0, box));
+ *   mass  device double[n];
+ *   n     1 .. 2^31 - 16;  box, r_s > 0 and finite;
+ *   ws    device workspace of ws_bytes >= og_pm_ws_bytes(plan), 256-byte
+ *         aligned; its first word is a status word (og_poll_status);
+ *   acc   device float[n][3] out, in the order of pos.
+ *   A plan holds one stream and one work area at a time: calls that share a
+ *   plan must not overlap (on different streams or threads).
+ *   Host-side argument errors return OG_EINVAL / OG_ENOSPACE.  Non-finite
+ *   positions or masses are skipped (acceleration 0) and flagged in the
+ *   status word (og_poll_status then returns OG_EINVAL).  The call is
+ *   asynchronous and can be captured in a CUDA graph.
+ */
+typedef struct og_pm_plan og_pm_plan;
+
+og_status og_pm_plan_create(int32_t ngrid, og_pm_plan** plan);
+void og_pm_plan_destroy(og_pm_plan* plan);
+size_t og_pm_ws_bytes(const og_pm_plan* plan);
+og_status og_pm_accel(og_pm_plan* plan, const double* pos, const double* mass, int64_t n, double box, double r_s,
+                      void* ws, size_t ws_bytes, float* acc, og_stream stream);
 
 /* Synchronise the stream and return the status recorded on the device in a
  * workspace or tree buffer (any buffer sized by the helpers above). */

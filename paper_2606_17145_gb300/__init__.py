@@ -26,7 +26,8 @@ _lib = None
 # 8 radix passes x (histogram, scan, scatter); permute + groups + root + 21
 # expand levels + 22 moment levels; one walk; adjoint walk + 22 push-down
 # levels + the particle gather.
-LAUNCHES_PER_CALL = {"keys_sort": 1 + 8 * 3, "tree_build": 3 + 21 + 22, "accel": 1, "adjoint": 1 + 22 + 1}
+LAUNCHES_PER_CALL = {"keys_sort": 1 + 8 * 3, "tree_build": 3 + 21 + 22, "accel": 1, "adjoint": 1 + 22 + 1,
+                     "pm": 3}  # pm: deposit, Green, interpolation (plus cuFFT's own kernels)
 
 
 def lib():
@@ -217,6 +218,49 @@ def shortrange_adjoint(tree: Tree, r_s: float, theta: float, w: torch.Tensor, st
     if check:
         _check(poll_status(ws, stream), "og_shortrange_adjoint (device)")
     return dpos, dmass
+
+
+class PMPlan:
+    """cuFFT plans for an N^3 long-range mesh (og_pm_plan_create); frees them when collected."""
+
+    def __init__(self, ngrid: int):
+        h = C.c_void_p()
+        _check(lib().og_pm_plan_create(int(ngrid), C.byref(h)), "og_pm_plan_create")
+        self.handle = h
+        self.ngrid = int(ngrid)
+        self._lib = lib()
+
+    @property
+    def ws_bytes(self) -> int:
+        return int(self._lib.og_pm_ws_bytes(self.handle))
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            self._lib.og_pm_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pm_accel(plan: PMPlan, pos: torch.Tensor, mass: torch.Tensor, box: float, r_s: float, stream=None,
+             check: bool = True, ws: torch.Tensor | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Long-range (PM) accelerations, float32 [n, 3] in the order of pos."""
+    _cuda(pos, torch.float64, (3,), "pos")
+    _cuda(mass, torch.float64, None, "mass")
+    n = pos.shape[0]
+    if ws is None:
+        ws = _workspace(plan.ws_bytes, pos.device)
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+    _check(lib().og_pm_accel(plan.handle, _ptr(pos), _ptr(mass), n, float(box), float(r_s), _ptr(ws), ws.numel(),
+                             _ptr(out), _stream(stream)), "og_pm_accel")
+    if check:
+        _check(poll_status(ws, stream), "og_pm_accel (device)")
+    return out
 
 
 class ShortRangeAccel(torch.autograd.Function):

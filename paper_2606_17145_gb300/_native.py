@@ -47,6 +47,11 @@ SIGNATURES = {
     "og_tree_node_count": (C.c_int64, [C.POINTER(og_tree), C.c_void_p]),
     "og_tree_copy_nodes": (C.c_int, [C.POINTER(og_tree)] + [C.c_void_p] * 9 + [C.c_void_p]),
     "og_status_str": (C.c_char_p, [C.c_int]),
+    "og_pm_plan_create": (C.c_int, [C.c_int32, C.POINTER(C.c_void_p)]),
+    "og_pm_plan_destroy": (None, [C.c_void_p]),
+    "og_pm_ws_bytes": (C.c_size_t, [C.c_void_p]),
+    "og_pm_accel": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_void_p,
+                              C.c_size_t, C.c_void_p, C.c_void_p]),
 }
 
 

@@ -8,6 +8,7 @@ no torch extension machinery: the library exports plain C symbols
 from __future__ import annotations
 
 import os
+import shutil
 import subprocess
 import sys
 
@@ -15,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libog.so")
-SOURCES = ["keys_sort.cu", "tree_build.cu", "walk.cu", "adjoint.cu", "og_abi.cu"]
+SOURCES = ["keys_sort.cu", "tree_build.cu", "walk.cu", "adjoint.cu", "og_abi.cu", "pm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -56,7 +57,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    # cuFFT for the PM mesh, found at run time through the toolkit's library
+    # directory (the same path on every machine this builds on)
+    nvcc_path = shutil.which(nvcc) or nvcc
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc_path))), "lib64")
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-L" + cudalib, "-lcufft", "-Xlinker", "-rpath=" + cudalib]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))

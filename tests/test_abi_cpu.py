@@ -79,3 +79,19 @@ def test_host_argument_checks(L):
     assert L.og_shortrange_adjoint(C.byref(hdr), 0.01, 0.5, 1, ws, ws, ws, 1, ws, 1 << 30, None) == N.OG_ENOTIMPL
     for code in range(7):
         assert L.og_status_str(code)
+
+
+def test_pm_host_argument_checks(L):
+    """The PM entry points refuse bad arguments on the host, before cuFFT or
+    any kernel is reached."""
+    from paper_2606_17145_gb300 import _native as N
+    h = C.c_void_p(1234)
+    for bad in (0, 4, 7, 1025, -8):
+        assert L.og_pm_plan_create(bad, C.byref(h)) == N.OG_EINVAL
+        assert h.value is None  # *plan is cleared on error
+    assert L.og_pm_plan_create(64, None) == N.OG_EINVAL
+    assert L.og_pm_ws_bytes(None) == 0
+    L.og_pm_plan_destroy(None)  # ignored
+    buf = C.create_string_buffer(1024)
+    p = C.cast(buf, C.c_void_p)
+    assert L.og_pm_accel(None, p, p, 10, 1.0, 0.01, p, 1024, p, None) == N.OG_EINVAL

@@ -13,49 +13,15 @@ sqrt(2) give 18-32 %.
 """
 import numpy as np
 import pytest
-from scipy.special import erfc
 
 import oracle
 from oracle import og_pm as P
+from pm_ref import ewald, long_series
 
 L = 1.0
 N = 32
 D = L / N
 R_S = 1.25 * D
-
-
-def _kvectors(kmax):
-    k1 = np.arange(-kmax, kmax + 1)
-    KX, KY, KZ = np.meshgrid(k1, k1, k1, indexing="ij")
-    kv = np.stack([KX.ravel(), KY.ravel(), KZ.ravel()], 1) * 2.0 * np.pi / L
-    k2 = (kv ** 2).sum(1)
-    keep = k2 > 0
-    return kv[keep], k2[keep]
-
-
-def long_series(d, r_s):
-    """Exact periodic long-range force of a unit mass at separation d:
-    -(4 pi / L^3) sum_k k exp(-k^2 r_s^2) / k^2 sin(k . d)."""
-    kmax = int(np.ceil(np.sqrt(45.0) / (2.0 * np.pi * r_s / L))) + 1
-    kv, k2 = _kvectors(kmax)
-    w = np.exp(-k2 * r_s ** 2) / k2 * np.sin(kv @ d)
-    return -(4.0 * np.pi / L ** 3) * (w[:, None] * kv).sum(0)
-
-
-def ewald(d, alpha):
-    """Periodic Newtonian force of a unit mass at separation d (Ewald sum with
-    splitting parameter alpha, neutralising background)."""
-    F = np.zeros(3)
-    for a in range(-2, 3):
-        for b in range(-2, 3):
-            for c in range(-2, 3):
-                s = d + L * np.array([a, b, c])
-                r = np.linalg.norm(s)
-                F -= (erfc(alpha * r) + 2.0 * alpha * r / np.sqrt(np.pi) * np.exp(-(alpha * r) ** 2)) * s / r ** 3
-    kv, k2 = _kvectors(int(np.ceil(7.0 * alpha * L / np.pi)) + 1)
-    w = np.exp(-k2 / (4.0 * alpha ** 2)) / k2 * np.sin(kv @ d)
-    F -= (4.0 * np.pi / L ** 3) * (w[:, None] * kv).sum(0)
-    return F
 
 
 def _pair(rng, r):
