@@ -40,20 +40,26 @@ namespace og {
 // Lower node index i0 in [0, N) and FP32 fraction f of one coordinate: the
 // same arithmetic in the deposit and the interpolation, so both see the same
 // weights.  u = (w N) / L; for a power-of-two side the division is the exact
-// multiply by 1 / L.
-__device__ __forceinline__ void cic_axis(double x, const BoxScale& B, int N, int& i0, float& f) {
+// multiply by 1 / L.  When L and N are both powers of two (log2N >= 0),
+// u = w 2^(log2N - e) exactly and floor / fraction come from the bits on the
+// integer pipe (the FP64 pipe is the scarce one); the FP64 form is the
+// definition and the fallback.
+__device__ __forceinline__ void cic_axis(double x, const BoxScale& B, int N, int log2N, int& i0, float& f) {
   const double w = wrap_coord(x, B);
-  const double wn = __dmul_rn(w, (double)N);
-  const double u = B.pow2 ? __dmul_rn(wn, B.invL) : __ddiv_rn(wn, B.L);
-  int i = __double2int_rd(u);
-  f = __double2float_rn(__dsub_rn(u, (double)i));
+  int i;
+  if (!(log2N >= 0 && B.pow2 && cic_bits((uint64_t)__double_as_longlong(w), B.e - log2N, i, f))) {
+    const double wn = __dmul_rn(w, (double)N);
+    const double u = B.pow2 ? __dmul_rn(wn, B.invL) : __ddiv_rn(wn, B.L);
+    i = __double2int_rd(u);
+    f = __double2float_rn(__dsub_rn(u, (double)i));
+  }
   if (i >= N) i -= N;  // w == L
   if (i < 0) i += N;   // w rounded to -0.x ulp: node N - 1, fraction near 1 (as floor and mod give)
   i0 = i;
 }
 
 __global__ void k_pm_deposit(const double* __restrict__ pos, const double* __restrict__ mass, int64_t n,
-                             BoxScale B, int N, float* __restrict__ R, StatusBlock* sb) {
+                             BoxScale B, int N, int log2N, float* __restrict__ R, StatusBlock* sb) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const double x0 = pos[3 * p], x1 = pos[3 * p + 1], x2 = pos[3 * p + 2];
     const double m = mass[p];
@@ -63,9 +69,9 @@ __global__ void k_pm_deposit(const double* __restrict__ pos, const double* __res
     }
     int ix, iy, iz;
     float fx, fy, fz;
-    cic_axis(x0, B, N, ix, fx);
-    cic_axis(x1, B, N, iy, fy);
-    cic_axis(x2, B, N, iz, fz);
+    cic_axis(x0, B, N, log2N, ix, fx);
+    cic_axis(x1, B, N, log2N, iy, fy);
+    cic_axis(x2, B, N, log2N, iz, fz);
     const int jx = ix + 1 == N ? 0 : ix + 1, jy = iy + 1 == N ? 0 : iy + 1, jz = iz + 1 == N ? 0 : iz + 1;
     const float mf = (float)m;
     const float wx[2] = {1.0f - fx, fx}, wy[2] = {1.0f - fy, fy}, wz[2] = {1.0f - fz, fz};
@@ -80,37 +86,40 @@ __global__ void k_pm_deposit(const double* __restrict__ pos, const double* __res
   }
 }
 
-// One thread per complex coefficient of the R2C layout [N][N][N/2 + 1].
+__device__ __forceinline__ float pm_sinc(int k, int N) {
+  if (k == 0) return 1.0f;
+  const float t = (float)k / (float)N;
+  return sinpif(t) / (3.14159265358979323846f * t);
+}
+
+// The R2C layout [N][N][N/2 + 1]: a block takes whole rows (ix, iy), its
+// threads the kz of the row, so no index is divided per coefficient.
 __global__ void k_pm_green(cufftComplex* __restrict__ C, int N, float inv_box, float two_pi_over_box, float r_s) {
   const int H = N / 2 + 1;
-  const int64_t total = (int64_t)N * N * H;
   const float pi = 3.14159265358979323846f;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int kz = (int)(e % H);
-    const int64_t t = e / H;
-    const int iy = (int)(t % N), ix = (int)(t / N);
+  // 1 / D^3 (masses -> density) times 1 / N^3 (inverse transform) = 1 / L^3
+  const float c0 = -4.0f * pi * (inv_box * inv_box * inv_box);
+  const float q2 = two_pi_over_box * two_pi_over_box;
+  for (int row = blockIdx.x; row < N * N; row += gridDim.x) {
+    const int ix = row / N, iy = row - ix * N;
     const int kx = ix <= N / 2 ? ix : ix - N;
     const int ky = iy <= N / 2 ? iy : iy - N;
-    float g = 0.0f;
-    if (kx != 0 || ky != 0 || kz != 0) {
-      const float k2 = two_pi_over_box * two_pi_over_box * (float)(kx * kx + ky * ky + kz * kz);
-      float s = 1.0f;
-      const int kk[3] = {kx, ky, kz};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (kk[a] != 0) {
-          const float t1 = (float)kk[a] / (float)N;
-          s *= sinpif(t1) / (pi * t1);
-        }
+    const float sxy = pm_sinc(kx, N) * pm_sinc(ky, N);
+    const int kxy = kx * kx + ky * ky;
+    cufftComplex* Crow = C + (int64_t)row * H;
+    for (int kz = threadIdx.x; kz < H; kz += blockDim.x) {
+      float g = 0.0f;
+      if (kxy != 0 || kz != 0) {
+        const float k2 = q2 * (float)(kxy + kz * kz);
+        const float s = sxy * pm_sinc(kz, N);
+        const float s2 = s * s;
+        g = c0 * expf(-k2 * r_s * r_s) / (k2 * s2 * s2);
       }
-      const float s2 = s * s;
-      // 1 / D^3 (masses -> density) times 1 / N^3 (inverse transform) = 1 / L^3
-      g = -4.0f * pi * expf(-k2 * r_s * r_s) / (k2 * s2 * s2) * (inv_box * inv_box * inv_box);
+      cufftComplex v = Crow[kz];
+      v.x *= g;
+      v.y *= g;
+      Crow[kz] = v;
     }
-    cufftComplex v = C[e];
-    v.x *= g;
-    v.y *= g;
-    C[e] = v;
   }
 }
 
@@ -126,7 +135,7 @@ __device__ __forceinline__ float pm_diff(float m2, float m1, float p1, float p2)
   return -((2.0f / 3.0f) * (p1 - m1) - (1.0f / 12.0f) * (p2 - m2));
 }
 
-__global__ void k_pm_interp(const double* __restrict__ pos, int64_t n, BoxScale B, int N, float inv_D,
+__global__ void k_pm_interp(const double* __restrict__ pos, int64_t n, BoxScale B, int N, int log2N, float inv_D,
                             const float* __restrict__ P, float* __restrict__ acc) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const double x0 = pos[3 * p], x1 = pos[3 * p + 1], x2 = pos[3 * p + 2];
@@ -134,9 +143,9 @@ __global__ void k_pm_interp(const double* __restrict__ pos, int64_t n, BoxScale 
     if (finite_bits(x0) && finite_bits(x1) && finite_bits(x2)) {
       int ix, iy, iz;
       float fx, fy, fz;
-      cic_axis(x0, B, N, ix, fx);
-      cic_axis(x1, B, N, iy, fy);
-      cic_axis(x2, B, N, iz, fz);
+      cic_axis(x0, B, N, log2N, ix, fx);
+      cic_axis(x1, B, N, log2N, iy, fy);
+      cic_axis(x2, B, N, log2N, iz, fz);
       const float wx[2] = {1.0f - fx, fx}, wy[2] = {1.0f - fy, fy}, wz[2] = {1.0f - fz, fz};
 #pragma unroll
       for (int b = 0; b < 2; ++b)
@@ -271,18 +280,22 @@ og_status og_pm_accel(og_pm_plan* plan, const double* pos, const double* mass, i
   if (cudaMemsetAsync(W.sb, 0, sizeof(og::StatusBlock), s) != cudaSuccess) return OG_ECUDA;
   if (cudaMemsetAsync(W.R, 0, sizeof(float) * (size_t)N * N * N, s) != cudaSuccess) return OG_ECUDA;
   const og::BoxScale B = og::box_scale(box);
-  og::k_pm_deposit<<<pm_grid(n), 256, 0, s>>>(pos, mass, n, B, N, W.R, W.sb);
+  int log2N = -1;  // N a power of two: its exponent
+  for (int e = 0; e < 11; ++e)
+    if (N == (1 << e)) log2N = e;
+  og::k_pm_deposit<<<pm_grid(n), 256, 0, s>>>(pos, mass, n, B, N, log2N, W.R, W.sb);
   if (cudaGetLastError() != cudaSuccess) return OG_ECUDA;
   if (cufftSetStream(plan->r2c, s) != CUFFT_SUCCESS || cufftSetWorkArea(plan->r2c, W.work) != CUFFT_SUCCESS ||
       cufftExecR2C(plan->r2c, W.R, W.C) != CUFFT_SUCCESS)
     return OG_ECUDA;
-  const int64_t nc = (int64_t)N * N * (N / 2 + 1);
-  og::k_pm_green<<<pm_grid(nc), 256, 0, s>>>(W.C, N, (float)(1.0 / box), (float)(2.0 * M_PI / box), (float)r_s);
+  const int rows = N * N;
+  og::k_pm_green<<<(unsigned)(rows < 152 * 64 ? rows : 152 * 64), 128, 0, s>>>(W.C, N, (float)(1.0 / box),
+                                                                              (float)(2.0 * M_PI / box), (float)r_s);
   if (cudaGetLastError() != cudaSuccess) return OG_ECUDA;
   if (cufftSetStream(plan->c2r, s) != CUFFT_SUCCESS || cufftSetWorkArea(plan->c2r, W.work) != CUFFT_SUCCESS ||
       cufftExecC2R(plan->c2r, W.C, W.R) != CUFFT_SUCCESS)
     return OG_ECUDA;
-  og::k_pm_interp<<<pm_grid(n), 256, 0, s>>>(pos, n, B, N, (float)(N / box), W.R, acc);
+  og::k_pm_interp<<<pm_grid(n), 256, 0, s>>>(pos, n, B, N, log2N, (float)(N / box), W.R, acc);
   return cudaGetLastError() == cudaSuccess ? OG_OK : OG_ECUDA;
 }
 

@@ -98,6 +98,44 @@ OG_HD bool d2f_scaled(uint64_t b, int s, float& out) {
   return true;
 }
 
+// CIC node and fraction of u = x 2^-s, from the bits b of x >= 0:
+//   i0 = floor(u) and f = (float)(u - floor(u)),
+// the FP64 expressions of a mesh coordinate.  u - floor(u) is exact in FP64
+// (the low bits of the significand); f rounds it to 24 bits.  Applies for
+// x = 0 and for 2^-126 <= u < 2^31; returns false, writing nothing, otherwise
+// (negative, subnormal or non-finite x, or u out of that range).
+OG_HD bool cic_bits(uint64_t b, int s, int& i0, float& f) {
+  if (b == 0) {
+    i0 = 0;
+    f = 0.0f;
+    return true;
+  }
+  const int E = (int)(b >> 52);
+  if (E == 0 || E >= 2047) return false;
+  const int eu = E - 1023 - s;  // u = S 2^(eu - 52)
+  if (eu > 30) return false;
+  if (eu < 0) {  // u < 1
+    if (!d2f_scaled(b, s, f)) return false;
+    i0 = 0;
+    return true;
+  }
+  const uint64_t S = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
+  const int sh = 52 - eu;  // 22 .. 52
+  const uint64_t frac = S & ((1ull << sh) - 1ull);
+  i0 = (int)(S >> sh);
+  if (frac == 0) {
+    f = 0.0f;
+    return true;
+  }
+  const int lz = clz64(frac);  // >= 64 - sh
+  const uint64_t v = frac << lz;
+  const uint32_t m = (uint32_t)(v >> 40);
+  const uint32_t r = round_up(m, v & 0xffffffffffull, 40);
+  // frac 2^-sh lies in [2^(63 - lz - sh), 1): biased exponent 190 - lz - sh
+  f = float_from_bits(((uint32_t)(190 - lz - sh) << 23) + (m - 0x800000u) + r);
+  return true;
+}
+
 }  // namespace og
 
 namespace og {

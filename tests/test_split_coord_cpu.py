@@ -29,6 +29,13 @@ extern "C" void t_split(const double* x, long n, int s, float* hi, float* lo, in
     ok[i] = og::split_bits(b, s, hi[i], lo[i]) ? 1 : 0;
   }
 }
+extern "C" void t_cic(const double* x, long n, int s, int* i0, float* f, int* ok) {
+  for (long i = 0; i < n; ++i) {
+    uint64_t b;
+    std::memcpy(&b, &x[i], 8);
+    ok[i] = og::cic_bits(b, s, i0[i], f[i]) ? 1 : 0;
+  }
+}
 extern "C" void t_odd(const unsigned* v, const int* x, long n, double* out, int* ok) {
   for (long i = 0; i < n; ++i) ok[i] = og::double_odd_scaled(v[i], x[i], out[i]) ? 1 : 0;
 }
@@ -57,6 +64,7 @@ def lib(tmp_path_factory):
     L.t_split.argtypes = [P, ctypes.c_long, ctypes.c_int, P, P, P]
     L.t_d2f.argtypes = [P, ctypes.c_long, ctypes.c_int, P, P]
     L.t_odd.argtypes = [P, P, ctypes.c_long, P, P]
+    L.t_cic.argtypes = [P, ctypes.c_long, ctypes.c_int, P, P, P]
     return L
 
 
@@ -183,3 +191,31 @@ def test_odd_scaled_is_the_exact_cell_centre(lib):
     m = ok[:100000]
     centre = (q[m] + 0.5) * np.ldexp(1.0, e[m] - lev[m])
     np.testing.assert_array_equal(out[:100000][m], centre)
+
+
+@pytest.mark.parametrize("s", [0, -8, -10, 3])
+def test_cic_matches_fp64_floor_and_fraction(lib, s):
+    """Mesh coordinate u = x 2^-s (e.g. x N / L for L = 1, N = 2^8: s = -8):
+    i0 = floor(u) and f = (float)(u - floor(u)) as FP64 gives them."""
+    rng = np.random.default_rng(23 + abs(s))
+    u = np.concatenate([rng.random(200000) * 1024.0, rng.random(50000),
+                        np.arange(0, 1025, dtype=np.float64),                      # nodes: f = 0
+                        np.nextafter(np.arange(1, 1025, dtype=np.float64), 0),     # just below a node
+                        np.arange(0, 1024) + 0.5, rng.integers(0, 1024, 50000) + 2.0 ** -30,
+                        np.array([0.0, 2.0 ** -126, 2.0 ** -127, 5e-324, 2.0 ** 31, 2.0 ** 30 + 0.5,
+                                  np.inf, np.nan, -0.25, -0.0])])
+    x = np.ldexp(u, s)
+    x = np.ascontiguousarray(x)
+    i0 = np.zeros(x.shape, np.int32)
+    f = np.zeros(x.shape, np.float32)
+    ok = np.zeros(x.shape, np.int32)
+    lib.t_cic(_ptr(x), x.size, s, _ptr(i0), _ptr(f), _ptr(ok))
+    ok = ok.astype(bool)
+    with np.errstate(invalid="ignore"):
+        uu = np.ldexp(x, -s)
+        applies = (x == 0) & ~np.signbit(x) | (np.isfinite(uu) & (uu >= 2.0 ** -126) & (uu < 2.0 ** 31)
+                                              & (x >= 2.0 ** -1022))
+    np.testing.assert_array_equal(ok, applies)
+    fl = np.floor(uu[ok])
+    np.testing.assert_array_equal(i0[ok], fl.astype(np.int64))
+    np.testing.assert_array_equal(f[ok].view(np.uint32), (uu[ok] - fl).astype(np.float32).view(np.uint32))
