@@ -500,6 +500,34 @@ def main():
     pm_ms = max_over_ranks(sum(pm_times) / len(pm_times), ws, dev)
     plan.close()
 
+    # one device-resident kick-drift-kick step (kick, drift, keys, tree, FP32
+    # walk, PM mesh, kick) on copies of the inputs; reported beside the line,
+    # never in place of it
+    kdk = None
+    try:
+        vel0 = torch.zeros_like(pos)
+        S = og.TreePMStepper(pos.clone(), vel0, mass, eps, w.box, w.r_s, args.theta, pm_n)
+        dt_k = 1e-4
+        for _ in range(args.warmup):
+            S.step(dt_k)
+        kt = []
+        for _ in range(max(1, min(args.steps, 10))):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            S.step(dt_k)
+            e1.record()
+            torch.cuda.synchronize()
+            kt.append(e0.elapsed_time(e1))
+        S.close()
+        kdk_ms = max_over_ranks(sum(kt) / len(kt), ws, dev)
+        kdk = {"ms": kdk_ms, "particles_per_s": ws * n / (kdk_ms * 1e-3), "ngrid": pm_n,
+               "what": "TreePMStepper.step: kick, drift, keys + sort, tree, FP32 walk, PM mesh, kick; "
+                       "stream launches (no graph), L2 flushed"}
+    except Exception as e:  # the headline line must still be printed
+        kdk = {"error": f"{type(e).__name__}: {e}"}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -522,6 +550,7 @@ def main():
                  "same_interactions": inter64 == interactions,
                  "fp32_speedup": f64_ms / pms["accel_fp32"], "fp32_vs_fp64": fp32_vs_fp64},
         "wall_s": wall,
+        "kdk_step": kdk,
         "pm": {"ngrid": pm_n, "ms": pm_ms, "particles_per_s": ws * n / (pm_ms * 1e-3),
                "what": "og_pm_accel: CIC deposit, cuFFT R2C, Green's function, cuFFT C2R, "
                        "difference + interpolation; FP32 mesh; timed apart from the step, L2 flushed"},

@@ -11,6 +11,7 @@
  *   og_shortrange_accel   warp-coherent Barnes-Hut walk (FP32 + Kahan, or FP64)
  *   og_shortrange_adjoint gradient of L = sum_i w_i . a_i with frozen decisions
  *   og_pm_accel           the long-range complement on a particle mesh
+ *   og_kick / og_drift    the leapfrog step's kick and drift
  *
  * Physics conventions (G = 1, attractive, code units):
  *   a_i = -sum_s m_s K_h(r) f(r) d,  d = x_i - x_s (periodic minimum image),
@@ -278,6 +279,25 @@ void og_pm_plan_destroy(og_pm_plan* plan);
 size_t og_pm_ws_bytes(const og_pm_plan* plan);
 og_status og_pm_accel(og_pm_plan* plan, const double* pos, const double* mass, int64_t n, double box, double r_s,
                       void* ws, size_t ws_bytes, float* acc, og_stream stream);
+
+/*
+ * Leapfrog kick and drift (the paper's step drifts every particle at its
+ * start and kicks with the new gravity, Sec. 2.1).  A kick-drift-kick step
+ * is og_kick(dt / 2), og_drift(dt), the forces (og_keys_sort,
+ * og_tree_build, og_shortrange_accel, og_pm_accel), og_kick(dt / 2).
+ *
+ * og_kick  -- vel += dt (acc_a + acc_b), componentwise in FP64.
+ *   vel    device double[n][3], updated in place;
+ *   acc_a  device float[n][3] (e.g. the FP32 walk's output);
+ *   acc_b  device float[n][3] or NULL (e.g. og_pm_accel's output).
+ * og_drift -- pos += dt vel; positions are not wrapped (every force call
+ *   wraps them itself).
+ *   pos    device double[n][3], updated in place;  vel device double[n][3].
+ * Both: 1 <= n <= 2^31 - 16, dt finite, else OG_EINVAL; asynchronous on
+ * the stream; OG_ECUDA if the launch fails.
+ */
+og_status og_kick(double* vel, const float* acc_a, const float* acc_b, int64_t n, double dt, og_stream stream);
+og_status og_drift(double* pos, const double* vel, int64_t n, double dt, og_stream stream);
 
 /* Synchronise the stream and return the status recorded on the device in a
  * workspace or tree buffer (any buffer sized by the helpers above). */

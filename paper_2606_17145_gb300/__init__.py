@@ -27,7 +27,7 @@ _lib = None
 # expand levels + 22 moment levels; one walk; adjoint walk + 22 push-down
 # levels + the particle gather.
 LAUNCHES_PER_CALL = {"keys_sort": 1 + 8 * 3, "tree_build": 3 + 21 + 22, "accel": 1, "adjoint": 1 + 22 + 1,
-                     "pm": 3}  # pm: deposit, Green, interpolation (plus cuFFT's own kernels)
+                     "pm": 3, "kick": 1, "drift": 1}  # pm: deposit, Green, interpolation (plus cuFFT's kernels)
 
 
 def lib():
@@ -261,6 +261,74 @@ def pm_accel(plan: PMPlan, pos: torch.Tensor, mass: torch.Tensor, box: float, r_
     if check:
         _check(poll_status(ws, stream), "og_pm_accel (device)")
     return out
+
+
+def kick(vel: torch.Tensor, acc_a: torch.Tensor, acc_b: torch.Tensor | None, dt: float, stream=None):
+    """vel += dt (acc_a + acc_b) in place (og_kick); acc_b may be None."""
+    _cuda(vel, torch.float64, (3,), "vel")
+    _cuda(acc_a, torch.float32, (3,), "acc_a")
+    if acc_b is not None:
+        _cuda(acc_b, torch.float32, (3,), "acc_b")
+    _check(lib().og_kick(_ptr(vel), _ptr(acc_a), _ptr(acc_b), vel.shape[0], float(dt), _stream(stream)), "og_kick")
+
+
+def drift(pos: torch.Tensor, vel: torch.Tensor, dt: float, stream=None):
+    """pos += dt vel in place (og_drift)."""
+    _cuda(pos, torch.float64, (3,), "pos")
+    _cuda(vel, torch.float64, (3,), "vel")
+    _check(lib().og_drift(_ptr(pos), _ptr(vel), pos.shape[0], float(dt), _stream(stream)), "og_drift")
+
+
+class TreePMStepper:
+    """Device-resident TreePM kick-drift-kick steps: positions, velocities,
+    accelerations and every workspace stay on the GPU; each step rebuilds the
+    keys and the tree and runs the FP32 walk and the PM mesh.  All buffers are
+    allocated here, none in step()."""
+
+    def __init__(self, pos: torch.Tensor, vel: torch.Tensor, mass: torch.Tensor, eps, box: float, r_s: float,
+                 theta: float, ngrid: int, p=None):
+        _cuda(pos, torch.float64, (3,), "pos")
+        _cuda(vel, torch.float64, (3,), "vel")
+        _cuda(mass, torch.float64, None, "mass")
+        L = lib()
+        dev = pos.device
+        n = pos.shape[0]
+        self.pos, self.vel, self.mass, self.eps = pos, vel, mass, eps
+        self.box, self.r_s, self.theta = float(box), float(r_s), float(theta)
+        self.p = p or params()
+        self.ws_keys = _workspace(L.og_keys_sort_ws_bytes(n), dev)
+        self.keys = torch.empty(n, dtype=torch.int64, device=dev)
+        self.order = torch.empty(n, dtype=torch.int32, device=dev)
+        self.tree_mem = _workspace(L.og_tree_bytes(n, C.byref(self.p)), dev)
+        self.acc_s = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        self.acc_l = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        self.total = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.plan = PMPlan(ngrid)
+        self.ws_pm = _workspace(self.plan.ws_bytes, dev)
+        self.ws_acc = None
+        self.forces(check=True)
+
+    def forces(self, check: bool = False, stream=None):
+        """Short-range (walk) and long-range (mesh) accelerations at the current positions."""
+        keys_sort(self.pos, self.box, stream=stream, check=check, ws=self.ws_keys, keys=self.keys, order=self.order)
+        tree = tree_build(self.keys, self.order, self.pos, self.mass, self.eps, self.box, p=self.p, stream=stream,
+                          check=check, mem=self.tree_mem)
+        if self.ws_acc is None:
+            self.ws_acc = _workspace(lib().og_accel_ws_bytes(C.byref(tree.header), 0), self.pos.device)
+        shortrange_accel(tree, self.r_s, self.theta, stream=stream, check=check, ws=self.ws_acc, out=self.acc_s,
+                         total=self.total)
+        pm_accel(self.plan, self.pos, self.mass, self.box, self.r_s, stream=stream, check=check, ws=self.ws_pm,
+                 out=self.acc_l)
+
+    def step(self, dt: float, check: bool = False, stream=None):
+        """One kick-drift-kick step of length dt."""
+        kick(self.vel, self.acc_s, self.acc_l, 0.5 * dt, stream)
+        drift(self.pos, self.vel, dt, stream)
+        self.forces(check=check, stream=stream)
+        kick(self.vel, self.acc_s, self.acc_l, 0.5 * dt, stream)
+
+    def close(self):
+        self.plan.close()
 
 
 class ShortRangeAccel(torch.autograd.Function):

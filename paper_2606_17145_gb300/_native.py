@@ -52,6 +52,8 @@ SIGNATURES = {
     "og_pm_ws_bytes": (C.c_size_t, [C.c_void_p]),
     "og_pm_accel": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_double, C.c_void_p,
                               C.c_size_t, C.c_void_p, C.c_void_p]),
+    "og_kick": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p]),
+    "og_drift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p]),
 }
 
 
