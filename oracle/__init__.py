@@ -6,8 +6,9 @@ benchmark's CPU-baseline / reference leg import this package.  The product
 path never calls it and has no CPU fallback.
 
 The PM long-range complement has its own numpy FP64 oracle in ``og_pm.py``
-(``from oracle import og_pm``), and the kick-drift-kick step one in
-``og_kdk.py``.
+(``from oracle import og_pm``), the kick-drift-kick step one in
+``og_kdk.py``, and the SPH density / smoothing-length iteration one in
+``og_sph.py``.
 
 ``build()`` compiles the C file with gcc (``-O2 -ffp-contract=off``: no fused
 multiply-add, so every FP64 decision formula is evaluated exactly as written).
