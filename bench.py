@@ -528,6 +528,29 @@ def main():
     except Exception as e:  # the headline line must still be printed
         kdk = {"error": f"{type(e).__name__}: {e}"}
 
+    # SPH density and smoothing length on the same tree (first version: one
+    # thread per particle, FP64), reported beside the line
+    sph = None
+    try:
+        n_ngb = 32.0
+        og.sph_density(tree, n_ngb)  # warm-up, checked
+        st = []
+        for _ in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            og.sph_density(tree, n_ngb, check=False)
+            e1.record()
+            torch.cuda.synchronize()
+            st.append(e0.elapsed_time(e1))
+        sph_ms = max_over_ranks(sum(st) / len(st), ws, dev)
+        sph = {"ms": sph_ms, "particles_per_s": ws * n / (sph_ms * 1e-3), "n_ngb": n_ngb,
+               "what": "og_sph_density: per-particle tree gather, bisection of h, density; FP64, one thread "
+                       "per particle"}
+    except Exception as e:  # the headline line must still be printed
+        sph = {"error": f"{type(e).__name__}: {e}"}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -551,6 +574,7 @@ def main():
                  "fp32_speedup": f64_ms / pms["accel_fp32"], "fp32_vs_fp64": fp32_vs_fp64},
         "wall_s": wall,
         "kdk_step": kdk,
+        "sph_density": sph,
         "pm": {"ngrid": pm_n, "ms": pm_ms, "particles_per_s": ws * n / (pm_ms * 1e-3),
                "what": "og_pm_accel: CIC deposit, cuFFT R2C, Green's function, cuFFT C2R, "
                        "difference + interpolation; FP32 mesh; timed apart from the step, L2 flushed"},

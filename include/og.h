@@ -12,6 +12,7 @@
  *   og_shortrange_adjoint gradient of L = sum_i w_i . a_i with frozen decisions
  *   og_pm_accel           the long-range complement on a particle mesh
  *   og_kick / og_drift    the leapfrog step's kick and drift
+ *   og_sph_density        SPH density and smoothing length on the same tree
  *
  * Physics conventions (G = 1, attractive, code units):
  *   a_i = -sum_s m_s K_h(r) f(r) d,  d = x_i - x_s (periodic minimum image),
@@ -298,6 +299,27 @@ og_status og_pm_accel(og_pm_plan* plan, const double* pos, const double* mass, i
  */
 og_status og_kick(double* vel, const float* acc_a, const float* acc_b, int64_t n, double dt, og_stream stream);
 og_status og_drift(double* pos, const double* vel, int64_t n, double dt, og_stream stream);
+
+/*
+ * SPH density and smoothing length on the tree (the paper's SPH density
+ * module iterates h until the sphere holds a fixed number of neighbours,
+ * Sec. 2.1).  With the cubic spline W of support h:
+ *   rho_i = sum_j m_j W(r_ij, h_i), the particle itself included, and
+ *   h_i is the root of (4 pi / 3) h^3 sum_j W(r_ij, h) = n_ngb
+ *   (periodic minimum image; h < box / 2).
+ * og_sph_ws_bytes -- workspace bytes (a status block).
+ * og_sph_density  -- t: a tree from og_tree_build (its positions and masses);
+ *   n_ngb > 0; ws of ws_bytes >= og_sph_ws_bytes(), 256-byte aligned;
+ *   outputs in the original particle order: h double[n], rho double[n],
+ *   ngb int32[n] (neighbours strictly inside h, self excluded).
+ *   A particle whose h cannot be bracketed below box / 2, or whose neighbour
+ *   gather keeps overflowing, gets NaN / -1 and sets a status bit
+ *   (og_poll_status returns OG_EWALK; a corrupt tree gives OG_ETREE).
+ *   Asynchronous on the stream.
+ */
+size_t og_sph_ws_bytes(void);
+og_status og_sph_density(const og_tree* t, double n_ngb, void* ws, size_t ws_bytes, double* h, double* rho,
+                         int32_t* ngb, og_stream stream);
 
 /* Synchronise the stream and return the status recorded on the device in a
  * workspace or tree buffer (any buffer sized by the helpers above). */

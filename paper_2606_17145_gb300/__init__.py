@@ -27,7 +27,7 @@ _lib = None
 # expand levels + 22 moment levels; one walk; adjoint walk + 22 push-down
 # levels + the particle gather.
 LAUNCHES_PER_CALL = {"keys_sort": 1 + 8 * 3, "tree_build": 3 + 21 + 22, "accel": 1, "adjoint": 1 + 22 + 1,
-                     "pm": 3, "kick": 1, "drift": 1}  # pm: deposit, Green, interpolation (plus cuFFT's kernels)
+                     "pm": 3, "kick": 1, "drift": 1, "sph": 1}  # pm: deposit, Green, interpolation (plus cuFFT's kernels)
 
 
 def lib():
@@ -277,6 +277,24 @@ def drift(pos: torch.Tensor, vel: torch.Tensor, dt: float, stream=None):
     _cuda(pos, torch.float64, (3,), "pos")
     _cuda(vel, torch.float64, (3,), "vel")
     _check(lib().og_drift(_ptr(pos), _ptr(vel), pos.shape[0], float(dt), _stream(stream)), "og_drift")
+
+
+def sph_density(tree: Tree, n_ngb: float, stream=None, check: bool = True, ws: torch.Tensor | None = None):
+    """SPH smoothing lengths, densities and neighbour counts (og_sph_density),
+    in the original particle order: (h float64 [n], rho float64 [n], ngb int32 [n])."""
+    L = lib()
+    dev = tree.mem.device
+    n = tree.n
+    if ws is None:
+        ws = _workspace(L.og_sph_ws_bytes(), dev)
+    h = torch.empty(n, dtype=torch.float64, device=dev)
+    rho = torch.empty(n, dtype=torch.float64, device=dev)
+    ngb = torch.empty(n, dtype=torch.int32, device=dev)
+    _check(L.og_sph_density(C.byref(tree.header), float(n_ngb), _ptr(ws), ws.numel(), _ptr(h), _ptr(rho), _ptr(ngb),
+                            _stream(stream)), "og_sph_density")
+    if check:
+        _check(poll_status(ws, stream), "og_sph_density (device)")
+    return h, rho, ngb
 
 
 class TreePMStepper:

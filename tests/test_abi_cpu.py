@@ -95,3 +95,14 @@ def test_pm_host_argument_checks(L):
     buf = C.create_string_buffer(1024)
     p = C.cast(buf, C.c_void_p)
     assert L.og_pm_accel(None, p, p, 10, 1.0, 0.01, p, 1024, p, None) == N.OG_EINVAL
+
+
+def test_sph_and_integrator_host_argument_checks(L):
+    from paper_2606_17145_gb300 import _native as N
+    assert L.og_sph_ws_bytes() >= 256
+    buf = C.create_string_buffer(1024)
+    p = C.cast(buf, C.c_void_p)
+    assert L.og_sph_density(None, 32.0, p, 1024, p, p, p, None) == N.OG_ETREE
+    assert L.og_kick(None, p, None, 10, 0.1, None) == N.OG_EINVAL
+    assert L.og_kick(p, p, None, 0, 0.1, None) == N.OG_EINVAL
+    assert L.og_drift(p, p, 10, float("nan"), None) == N.OG_EINVAL
