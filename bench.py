@@ -521,12 +521,16 @@ def main():
             torch.cuda.synchronize()
             kt.append(e0.elapsed_time(e1))
         S.close()
-        kdk_ms = max_over_ranks(sum(kt) / len(kt), ws, dev)
-        kdk = {"ms": kdk_ms, "particles_per_s": ws * n / (kdk_ms * 1e-3), "ngrid": pm_n,
-               "what": "TreePMStepper.step: kick, drift, keys + sort, tree, FP32 walk, PM mesh, kick; "
-                       "stream launches (no graph), L2 flushed"}
+        kdk_local = sum(kt) / len(kt)
     except Exception as e:  # the headline line must still be printed
-        kdk = {"error": f"{type(e).__name__}: {e}"}
+        kdk_local, kdk = float("inf"), {"error": f"{type(e).__name__}: {e}"}
+    # every rank takes part in the max, whether or not its leg failed
+    kdk_ms = max_over_ranks(kdk_local, ws, dev)
+    if kdk is None:
+        kdk = ({"ms": kdk_ms, "particles_per_s": ws * n / (kdk_ms * 1e-3), "ngrid": pm_n,
+                "what": "TreePMStepper.step: kick, drift, keys + sort, tree, FP32 walk, PM mesh, kick; "
+                        "stream launches (no graph), L2 flushed"}
+               if kdk_ms < float("inf") else {"error": "failed on another rank"})
 
     # SPH density and smoothing length on the same tree (first version: one
     # thread per particle, FP64), reported beside the line
@@ -544,12 +548,15 @@ def main():
             e1.record()
             torch.cuda.synchronize()
             st.append(e0.elapsed_time(e1))
-        sph_ms = max_over_ranks(sum(st) / len(st), ws, dev)
-        sph = {"ms": sph_ms, "particles_per_s": ws * n / (sph_ms * 1e-3), "n_ngb": n_ngb,
-               "what": "og_sph_density: per-particle tree gather, bisection of h, density; FP64, one thread "
-                       "per particle"}
+        sph_local = sum(st) / len(st)
     except Exception as e:  # the headline line must still be printed
-        sph = {"error": f"{type(e).__name__}: {e}"}
+        sph_local, sph = float("inf"), {"error": f"{type(e).__name__}: {e}"}
+    sph_ms = max_over_ranks(sph_local, ws, dev)
+    if sph is None:
+        sph = ({"ms": sph_ms, "particles_per_s": ws * n / (sph_ms * 1e-3), "n_ngb": 32.0,
+                "what": "og_sph_density: per-particle tree gather, bisection of h, density; FP64, one thread "
+                        "per particle"}
+               if sph_ms < float("inf") else {"error": "failed on another rank"})
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
