@@ -4,7 +4,8 @@
  * The library computes the short-range part of a TreePM gravity force in a
  * periodic box, i.e. the Barnes-Hut tree walk the paper ports to GPUs
  * (Sec. 2: a tree walk per active particle; Sec. 3.1: Barnes-Hut for the
- * short-range force, long-range PM on the host).  The steps are
+ * short-range force, long-range PM on the host), and around it the
+ * long-range mesh, the leapfrog step and the SPH density.  The steps are
  *
  *   og_keys_sort          63-bit Peano-Hilbert keys + stable radix sort
  *   og_tree_build         octree with monopole moments, level by level
@@ -29,7 +30,8 @@
  * Memory and ownership.  The caller owns every buffer.  Unless stated
  * otherwise, pointers are DEVICE pointers on the current CUDA device; the
  * og_params and og_tree structs are HOST structs.  The library never
- * allocates or frees device memory and never synchronises, except in
+ * allocates or frees device memory (except cuFFT, for its own tables, when
+ * og_pm_plan_create makes a plan) and never synchronises, except in
  * og_poll_status / og_tree_node_count.  Every call is asynchronous on the
  * given stream.  Workspaces are sized by the *_ws_bytes / og_tree_bytes
  * helpers and must be 256-byte aligned.
