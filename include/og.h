@@ -323,6 +323,29 @@ size_t og_sph_ws_bytes(void);
 og_status og_sph_density(const og_tree* t, double n_ngb, void* ws, size_t ws_bytes, double* h, double* rho,
                          int32_t* ngb, og_stream stream);
 
+/*
+ * og_probe_pipe -- throughput probe of one SM pipe (measurement helper).
+ *
+ * The paper has no counterpart: the walks are bound by the FP32 pipe, the
+ * special-function unit and (the comparison variant) the FP64 pipe, and the
+ * roofline fractions reported for them need those pipes' rates as measured on
+ * the device, not unit counts.  One launch runs independent dependency chains
+ * of one instruction kind on every SM (4 blocks of 256 threads per SM); the
+ * caller times it with CUDA events on the stream and divides *ops by the time.
+ *
+ * kind   OG_PROBE_FFMA  fma.rn.f32 (ops = FMAs; flops = 2 ops)
+ *        OG_PROBE_FFMA2 fma.rn.f32x2, two FMAs per instruction (ops = FMAs)
+ *        OG_PROBE_MUFU  alternating rsqrt.approx / ex2.approx (ops = MUFU ops)
+ *        OG_PROBE_DFMA  fma.rn.f64 (ops = FMAs)
+ * iters  1 .. 2^24; each thread performs iters x 128 operations
+ *        (x 2 for FFMA2); about 2^12 gives a launch of some milliseconds
+ * sink   device float[1]; never written in practice (it keeps the chains live)
+ * ops    host out: operations the launch performs
+ * Returns OG_EINVAL for a bad kind or iters, OG_ECUDA if the launch fails.
+ */
+enum { OG_PROBE_FFMA = 0, OG_PROBE_FFMA2 = 1, OG_PROBE_MUFU = 2, OG_PROBE_DFMA = 3 };
+og_status og_probe_pipe(int32_t kind, int32_t iters, float* sink, uint64_t* ops, og_stream stream);
+
 /* Synchronise the stream and return the status recorded on the device in a
  * workspace or tree buffer (any buffer sized by the helpers above). */
 og_status og_poll_status(const void* buf, og_stream stream);

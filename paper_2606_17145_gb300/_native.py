@@ -55,6 +55,7 @@ SIGNATURES = {
     "og_kick": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p]),
     "og_drift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p]),
     "og_sph_ws_bytes": (C.c_size_t, []),
+    "og_probe_pipe": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_uint64), C.c_void_p]),
     "og_sph_density": (C.c_int, [C.POINTER(og_tree), C.c_double, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]),
 }

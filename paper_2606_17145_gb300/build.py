@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libog.so")
-SOURCES = ["keys_sort.cu", "tree_build.cu", "walk.cu", "adjoint.cu", "og_abi.cu", "pm.cu", "integrate.cu", "sph.cu"]
+SOURCES = ["keys_sort.cu", "tree_build.cu", "walk.cu", "adjoint.cu", "og_abi.cu", "pm.cu", "integrate.cu", "sph.cu", "probes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

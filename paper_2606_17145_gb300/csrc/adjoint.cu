@@ -76,10 +76,10 @@ __global__ void k_adj_particles(TreeDev T, AdjWs W, double L, double* __restrict
 
 cudaError_t launch_adjoint_push(const TreeDev& T, const AdjWs& W, double L, double* dpos, double* dmass,
                                 cudaStream_t s) {
-  const unsigned grid = 152 * 8;
+  const unsigned grid = grid_cap(8);
   for (int lev = 0; lev <= kMaxLevel; ++lev) k_adj_down<<<grid, 256, 0, s>>>(T, W, lev, 1.0 / L);
   int64_t pg = (T.n + 255) / 256;
-  if (pg > 152 * 32) pg = 152 * 32;
+  if (pg > grid_cap(32)) pg = grid_cap(32);
   k_adj_particles<<<(unsigned)pg, 256, 0, s>>>(T, W, L, dpos, dmass);
   return cudaGetLastError();
 }

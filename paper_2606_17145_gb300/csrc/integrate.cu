@@ -35,7 +35,7 @@ constexpr int64_t kIntMaxN = 0x7ffffff0LL;
 
 unsigned int_grid(int64_t items) {
   int64_t g = (items + 255) / 256;
-  if (g > 152 * 32) g = 152 * 32;
+  if (g > og::grid_cap(32)) g = og::grid_cap(32);
   return (unsigned)(g > 0 ? g : 1);
 }
 

@@ -240,7 +240,7 @@ cudaError_t launch_keys_sort(const double* pos, int64_t n, double L, uint64_t* k
                              const SortWs& W, cudaStream_t s) {
   const int kb = 256;
   int64_t kgrid = (n + kb - 1) / kb;
-  if (kgrid > 152 * 64) kgrid = 152 * 64;
+  if (kgrid > grid_cap(64)) kgrid = grid_cap(64);
   k_keys<<<(unsigned)kgrid, kb, 0, s>>>(pos, n, box_scale(L), keys_out, order_out, W.sb);
   uint64_t* kin = keys_out;
   int32_t* vin = order_out;

@@ -325,6 +325,15 @@ struct WalkArgs {
   double* tgt;
 };
 
+// SM count of the current device (0 on error); grids are sized from it.
+int device_sm_count();
+
+// Grid cap: per_sm blocks on every SM of the current device.
+inline unsigned grid_cap(int per_sm) {
+  const int s = device_sm_count();
+  return (unsigned)((s > 0 ? s : 1) * per_sm);
+}
+
 cudaError_t launch_keys_sort(const double* pos, int64_t n, double L, uint64_t* keys_out, int32_t* order_out,
                              const SortWs& W, cudaStream_t s);
 cudaError_t launch_tree_build(const BuildArgs& A, cudaStream_t s);

@@ -216,7 +216,7 @@ bool pm_finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 unsigned pm_grid(int64_t items) {
   int64_t g = (items + 255) / 256;
-  if (g > 152 * 32) g = 152 * 32;
+  if (g > og::grid_cap(32)) g = og::grid_cap(32);
   return (unsigned)(g > 0 ? g : 1);
 }
 
@@ -289,7 +289,7 @@ og_status og_pm_accel(og_pm_plan* plan, const double* pos, const double* mass, i
       cufftExecR2C(plan->r2c, W.R, W.C) != CUFFT_SUCCESS)
     return OG_ECUDA;
   const int rows = N * N;
-  og::k_pm_green<<<(unsigned)(rows < 152 * 64 ? rows : 152 * 64), 128, 0, s>>>(W.C, N, (float)(1.0 / box),
+  og::k_pm_green<<<(unsigned)(rows < (int)og::grid_cap(64) ? rows : (int)og::grid_cap(64)), 128, 0, s>>>(W.C, N, (float)(1.0 / box),
                                                                               (float)(2.0 * M_PI / box), (float)r_s);
   if (cudaGetLastError() != cudaSuccess) return OG_ECUDA;
   if (cufftSetStream(plan->c2r, s) != CUFFT_SUCCESS || cufftSetWorkArea(plan->c2r, W.work) != CUFFT_SUCCESS ||

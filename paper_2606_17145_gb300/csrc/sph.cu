@@ -189,7 +189,7 @@ og_status og_sph_density(const og_tree* t, double n_ngb, void* ws, size_t ws_byt
   A.ngb_out = ngb;
   if (cudaMemsetAsync(A.wsb, 0, sizeof(og::StatusBlock), s) != cudaSuccess) return OG_ECUDA;
   int64_t grid = (t->n + 127) / 128;
-  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid > og::grid_cap(16)) grid = og::grid_cap(16);
   og::k_sph_density<<<(unsigned)grid, 128, 0, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? OG_OK : OG_ECUDA;
 }

@@ -259,16 +259,16 @@ __global__ void __launch_bounds__(256) k_moments(TreeDev T, int lev, BoxScale B)
 cudaError_t launch_tree_build(const BuildArgs& A, cudaStream_t s) {
   const TreeDev& T = A.T;
   int64_t grid = (T.n + 255) / 256;
-  if (grid > 152 * 32) grid = 152 * 32;
+  if (grid > grid_cap(32)) grid = grid_cap(32);
   const BoxScale B = box_scale(A.L);
   k_permute<<<(unsigned)grid, 256, 0, s>>>(A, B);
   int64_t ggrid = (T.ngroups + 127) / 128;
-  if (ggrid > 152 * 16) ggrid = 152 * 16;
+  if (ggrid > grid_cap(16)) ggrid = grid_cap(16);
   k_groups<<<(unsigned)ggrid, 128, 0, s>>>(T, B);
   k_root<<<1, 32, 0, s>>>(T, A.leaf_size);
   // Grids are fixed (the per-level node count lives on the device); blocks
   // stride over the level.
-  const unsigned egrid = 152 * 8;
+  const unsigned egrid = grid_cap(8);
   for (int lev = 0; lev < kMaxLevel; ++lev) k_expand<<<egrid, 256, 0, s>>>(T, A.keys, lev, A.leaf_size);
   for (int lev = kMaxLevel; lev >= 0; --lev) k_moments<<<egrid, 256, 0, s>>>(T, lev, B);
   return cudaGetLastError();
@@ -296,7 +296,7 @@ cudaError_t launch_copy_nodes(const TreeDev& T, int64_t m, int32_t* level, int32
                               int32_t* nchild, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   int64_t grid = (m + 255) / 256;
-  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid > grid_cap(16)) grid = grid_cap(16);
   k_copy_nodes<<<(unsigned)grid, 256, 0, s>>>(T, m, level, first, count, parent, mass, com, hmax, child_first,
                                               nchild);
   return cudaGetLastError();
