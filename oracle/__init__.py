@@ -90,10 +90,10 @@ def lib():
                                          C.c_void_p, C.c_void_p]
             L.orc_adjoint.restype = None
             L.orc_adjoint.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D, C.c_void_p,
-                                      C.c_int64, _D, _D]
+                                      C.c_int64, _D, _D, C.c_void_p, C.c_void_p]
             L.orc_fd.restype = None
             L.orc_fd.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D, _I64, C.c_int64,
-                                 C.c_double, C.c_double, _D, _D]
+                                 C.c_double, C.c_double, _D, _D, C.c_void_p]
             L.orc_loss.restype = C.c_double
             L.orc_loss.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D]
             _lib = L
@@ -227,7 +227,10 @@ class Tree:
         self._L.orc_walk_lists(self._h, rcut, theta, tg, tg.shape[0], off, kind.ctypes.data, ids.ctypes.data)
         return off, kind[: off[-1]], ids[: off[-1]]
 
-    def adjoint(self, r_s, rcut, theta, w, samples=None):
+    def adjoint(self, r_s, rcut, theta, w, samples=None, with_scale=False):
+        """dL/dx [ns,3], dL/dm [ns] of L = sum_i w_i . a_i (frozen decisions).
+        with_scale: also return the same sums over the absolute values of
+        their terms (the scale of any evaluation's rounding error)."""
         w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1, 3)
         if samples is None:
             ns = self.n
@@ -238,17 +241,25 @@ class Tree:
             sp = samples.ctypes.data
         dpos = np.zeros((ns, 3))
         dmass = np.zeros(ns)
-        self._L.orc_adjoint(self._h, r_s, rcut, theta, w.ravel(), sp, ns, dpos.ravel(), dmass)
-        return dpos, dmass
+        dpa = np.zeros((ns, 3)) if with_scale else None
+        dma = np.zeros(ns) if with_scale else None
+        self._L.orc_adjoint(self._h, r_s, rcut, theta, w.ravel(), sp, ns, dpos.ravel(), dmass,
+                            dpa.ctypes.data if with_scale else None, dma.ctypes.data if with_scale else None)
+        return (dpos, dmass, dpa, dma) if with_scale else (dpos, dmass)
 
-    def fd(self, r_s, rcut, theta, w, samples, hx=1e-6, hm_rel=1e-6):
+    def fd(self, r_s, rcut, theta, w, samples, hx=1e-6, hm_rel=1e-6, with_flags=False):
+        """Central differences of the frozen-list loss.  with_flags: also the
+        per-sample crossing flags (bit 0: a step moves an involved term across
+        its softening length, bit 1: across rcut)."""
         w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1, 3)
         samples = np.ascontiguousarray(samples, dtype=np.int64)
         ns = samples.shape[0]
         dpos = np.zeros((ns, 3))
         dmass = np.zeros(ns)
-        self._L.orc_fd(self._h, r_s, rcut, theta, w.ravel(), samples, ns, hx, hm_rel, dpos.ravel(), dmass)
-        return dpos, dmass
+        flags = np.zeros(ns, np.int32)
+        self._L.orc_fd(self._h, r_s, rcut, theta, w.ravel(), samples, ns, hx, hm_rel, dpos.ravel(), dmass,
+                       flags.ctypes.data)
+        return (dpos, dmass, flags) if with_flags else (dpos, dmass)
 
     def loss(self, r_s, rcut, theta, w) -> float:
         w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1, 3)

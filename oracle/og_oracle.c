@@ -719,9 +719,13 @@ static int orc_ancestors(const orc_tree* T, int64_t k, int64_t* anc) {
 }
 
 /* Analytic gradient for the sample particles (all particles if samples ==
- * NULL).  w is [n][3] in original order.  Outputs are per sample. */
+ * NULL).  w is [n][3] in original order.  Outputs are per sample.
+ * dpos_abs / dmass_abs (optional, may be NULL): the same sums taken over the
+ * absolute values of their terms, i.e. the scale against which the rounding
+ * error of any evaluation of these sums is measured (a sum of terms each
+ * computed with relative error e is off by at most e times this scale). */
 void orc_adjoint(void* hnd, double r_s, double rcut, double theta, const double* w, const int64_t* samples,
-                 int64_t ns, double* dpos, double* dmass) {
+                 int64_t ns, double* dpos, double* dmass, double* dpos_abs, double* dmass_abs) {
   const orc_tree* T = (const orc_tree*)hnd;
   int64_t n = T->n, M = T->nn;
   int all = samples == NULL;
@@ -742,6 +746,12 @@ void orc_adjoint(void* hnd, double r_s, double rcut, double theta, const double*
   double* Gp = (double*)calloc((size_t)n * 3, sizeof(double));
   double* Sp = (double*)calloc((size_t)n, sizeof(double));
   double* tgt = (double*)calloc((size_t)ns * 3, sizeof(double));
+  const int want_abs = dpos_abs != NULL || dmass_abs != NULL;
+  double* Gna = want_abs ? (double*)calloc((size_t)M * 3, sizeof(double)) : NULL;
+  double* Sna = want_abs ? (double*)calloc((size_t)M, sizeof(double)) : NULL;
+  double* Gpa = want_abs ? (double*)calloc((size_t)n * 3, sizeof(double)) : NULL;
+  double* Spa = want_abs ? (double*)calloc((size_t)n, sizeof(double)) : NULL;
+  double* tgta = want_abs ? (double*)calloc((size_t)ns * 3, sizeof(double)) : NULL;
   orc_list L = {0};
   for (int64_t i = 0; i < n; i++) {
     if (!mark[i]) continue;
@@ -766,6 +776,13 @@ void orc_adjoint(void* hnd, double r_s, double rcut, double theta, const double*
         for (int c = 0; c < 3; c++) Gp[3 * j + c] += Jw[c];
         Sp[j] += wg;
       }
+      if (want_abs) {
+        if (slot[i] >= 0) for (int c = 0; c < 3; c++) tgta[3 * slot[i] + c] += Ms * fabs(Jw[c]);
+        double* Ga = L.v[q].kind == 0 ? &Gna[3 * L.v[q].id] : &Gpa[3 * L.v[q].id];
+        double* Sa = L.v[q].kind == 0 ? &Sna[L.v[q].id] : &Spa[L.v[q].id];
+        for (int c = 0; c < 3; c++) Ga[c] += fabs(Jw[c]);
+        *Sa += fabs(wg);
+      }
     }
   }
   int64_t anc[64];
@@ -785,16 +802,36 @@ void orc_adjoint(void* hnd, double r_s, double rcut, double theta, const double*
     }
     for (int c = 0; c < 3; c++) dpos[3 * s + c] = dx[c];
     dmass[s] = dm;
+    if (want_abs) {
+      double ax[3], am = Spa[k];
+      for (int c = 0; c < 3; c++) ax[c] = tgta[3 * s + c] + mk * Gpa[3 * k + c];
+      for (int a = 0; a < na; a++) {
+        const orc_node* nd = &T->nodes[anc[a]];
+        const double* Ga = &Gna[3 * anc[a]];
+        for (int c = 0; c < 3; c++) {
+          ax[c] += mk * Ga[c];
+          am += Ga[c] * fabs(T->x[3 * k + c] - nd->com[c]);
+        }
+        am += Sna[anc[a]];
+      }
+      if (dpos_abs) for (int c = 0; c < 3; c++) dpos_abs[3 * s + c] = ax[c];
+      if (dmass_abs) dmass_abs[s] = am;
+    }
   }
   free(L.v); free(mark); free(sidx); free(slot); free(Gn); free(Sn); free(Gp); free(Sp); free(tgt);
+  free(Gna); free(Sna); free(Gpa); free(Spa); free(tgta);
 }
 
 /* Part of the loss that involves particle k, with k moved by dx (3-vector)
  * and its mass changed by dmk, holding every interaction list fixed.  Node
  * masses and centres of mass are updated for the change. */
+/* *cross (optional) gets bit 0 if an involved term's distance is on the other
+ * side of its softening length h than unperturbed, bit 1 if on the other side
+ * of rcut (the frozen lists keep the term either way; the kernel has a kink at
+ * h, so a central difference across it is only first-order accurate). */
 static double orc_local_loss(const orc_tree* T, int64_t k, const double* w, int64_t* off, int32_t* kind,
-                             int64_t* ids, const int64_t* tlist, int64_t nt, double r_s, const double dxk[3],
-                             double dmk) {
+                             int64_t* ids, const int64_t* tlist, int64_t nt, double r_s, double rcut,
+                             const double dxk[3], double dmk, int* cross) {
   double loss = 0.0;
   double mk = T->m[k];
   for (int64_t t = 0; t < nt; t++) {
@@ -830,12 +867,18 @@ static double orc_local_loss(const orc_tree* T, int64_t k, const double* w, int6
       }
       if (!involves) continue;
       double h = T->h[i] > hs ? T->h[i] : hs;
-      double d[3];
+      double d[3], dz[3];
       for (int c = 0; c < 3; c++) {
         double d0 = orc_mi(T->x[3 * i + c] - X[c], T->box);
+        dz[c] = d0;
         d[c] = d0 + (i == k ? dxk[c] : 0.0) - dX[c];
       }
       double r = sqrt(orc_norm2(d));
+      if (cross) {
+        double r0 = sqrt(orc_norm2(dz));
+        if ((r0 < h) != (r < h)) *cross |= 1;
+        if ((r0 < rcut) != (r < rcut)) *cross |= 2;
+      }
       double fac = -Mp * orc_F(r, h, r_s);
       loss += fac * ((wi[0] * d[0] + wi[1] * d[1]) + wi[2] * d[2]);
     }
@@ -844,9 +887,11 @@ static double orc_local_loss(const orc_tree* T, int64_t k, const double* w, int6
 }
 
 /* Central finite differences of the frozen-list loss for the sample
- * particles: position step hx (absolute), mass step hm_rel * m_k. */
+ * particles: position step hx (absolute), mass step hm_rel * m_k.
+ * flags (optional, may be NULL): per sample, bit 0 if a position step moves an
+ * involved term across its softening length h, bit 1 if across rcut. */
 void orc_fd(void* hnd, double r_s, double rcut, double theta, const double* w, const int64_t* samples, int64_t ns,
-            double hx, double hm_rel, double* dpos, double* dmass) {
+            double hx, double hm_rel, double* dpos, double* dmass, int32_t* flags) {
   const orc_tree* T = (const orc_tree*)hnd;
   int64_t n = T->n;
   double R = rcut * (1.0 + sqrt(3.0) * theta) * (1.0 + 1e-9) + 1e-12;
@@ -863,15 +908,17 @@ void orc_fd(void* hnd, double r_s, double rcut, double theta, const double* w, c
     int32_t* kind = (int32_t*)malloc(sizeof(int32_t) * (size_t)(off[nt] + 1));
     int64_t* ids = (int64_t*)malloc(sizeof(int64_t) * (size_t)(off[nt] + 1));
     orc_walk_lists(hnd, rcut, theta, tl, nt, off, kind, ids);
+    int cross = 0;
     for (int c = 0; c < 4; c++) {
       double dp[3] = {0, 0, 0}, dn[3] = {0, 0, 0}, mp = 0.0, mn = 0.0, step;
       if (c < 3) { dp[c] = hx; dn[c] = -hx; step = hx; }
       else { step = hm_rel * T->m[k]; mp = step; mn = -step; }
-      double Lp = orc_local_loss(T, k, w, off, kind, ids, tl, nt, r_s, dp, mp);
-      double Ln = orc_local_loss(T, k, w, off, kind, ids, tl, nt, r_s, dn, mn);
+      double Lp = orc_local_loss(T, k, w, off, kind, ids, tl, nt, r_s, rcut, dp, mp, &cross);
+      double Ln = orc_local_loss(T, k, w, off, kind, ids, tl, nt, r_s, rcut, dn, mn, &cross);
       double g = (Lp - Ln) / (2.0 * step);
       if (c < 3) dpos[3 * s + c] = g; else dmass[s] = g;
     }
+    if (flags) flags[s] = cross;
     free(off); free(kind); free(ids);
   }
   free(mark); free(tl);

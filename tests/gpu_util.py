@@ -56,3 +56,21 @@ def err_stats(a, ref):
     scale = np.sqrt(np.mean(np.sum(ref * ref, axis=1)))
     return dict(rms=float(np.sqrt(np.mean(r ** 2))), p99=float(np.percentile(r, 99)), max=float(r.max()),
                 med=float(np.median(r)), norm_max=float(np.linalg.norm(a - ref, axis=1).max() / scale))
+
+
+
+# FP32 terms: displacement rounding, rsqrt / ex2 approximations, the
+# short-range polynomial and a handful of products give each term a relative
+# error below about 2e-6; per-warp FP32 partial sums of up to 32 terms before
+# the FP64 accumulation add about as much.  A gradient component is therefore
+# within ~4e-6 of its terms' absolute sum; the tests allow 1e-5 of it.
+GRAD_TOL = 1e-5
+
+
+def grad_scaled_err(g, ref, scale):
+    """max over particles and components of |g - ref| / scale, where scale is
+    the oracle's sum of the absolute values of the terms of that component."""
+    g = np.asarray(g, dtype=np.float64).reshape(len(g), -1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(len(ref), -1)
+    sc = np.asarray(scale, dtype=np.float64).reshape(len(scale), -1)
+    return float((np.abs(g - ref) / np.maximum(sc, 1e-300)).max())

@@ -13,4 +13,7 @@ def fd_chunk(args):
     w = ics.make(name)
     T = oracle.Tree(w.pos, w.mass, 2.8 * w.eps)
     wt = w.w.astype(np.float32).astype(np.float64)
-    return T.fd(w.r_s, w.rcut, theta, wt, np.asarray(samples, dtype=np.int64), hx=1e-6, hm_rel=1e-6)
+    smp = np.asarray(samples, dtype=np.int64)
+    fp, fm, fl = T.fd(w.r_s, w.rcut, theta, wt, smp, hx=1e-6, hm_rel=1e-6, with_flags=True)
+    ap, am, sp, sm = T.adjoint(w.r_s, w.rcut, theta, wt, smp, with_scale=True)
+    return fp, fm, fl, ap, am, sp, sm

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import ics
-from gpu_util import device, err_stats, forward, og, torch
+from gpu_util import GRAD_TOL, device, err_stats, forward, grad_scaled_err, og, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -187,11 +187,12 @@ def test_dense_clump_adjoint(orc):
     dpos, dmass = m.shortrange_adjoint(tree, w.r_s, 0.5, torch.tensor(wt, dtype=torch.float32, device=dev))
     gp, gm = dpos.cpu().numpy(), dmass.cpu().numpy()
     s = np.arange(0, w.n, 13)
-    op, om = _oracle_tree(orc, w).adjoint(w.r_s, w.rcut, 0.5, wt, s)
+    op, om, pa, ma = _oracle_tree(orc, w).adjoint(w.r_s, w.rcut, 0.5, wt, s, with_scale=True)
     ep = np.abs(gp[s] - op).max() / np.abs(op).max()
     em = np.abs(gm[s] - om).max() / np.abs(om).max()
-    print("dense clump adjoint", ep, em)
+    print("dense clump adjoint", ep, em, grad_scaled_err(gp[s], op, pa), grad_scaled_err(gm[s], om, ma))
     assert ep < 2e-5 and em < 2e-5
+    assert grad_scaled_err(gp[s], op, pa) < GRAD_TOL and grad_scaled_err(gm[s], om, ma) < GRAD_TOL
 
 
 @pytest.mark.parametrize("name,scale,deep", [("nfw256", 24, 1), ("zoom8m", 20000, 3), ("uniform4096", None, 2)])
@@ -216,9 +217,10 @@ def test_single_range_pops_adjoint(orc):
     dpos, dmass = m.shortrange_adjoint(tree, w.r_s, 0.5, torch.tensor(wt, dtype=torch.float32, device=dev))
     gp, gm = dpos.cpu().numpy(), dmass.cpu().numpy()
     s = np.arange(0, w.n, 11)
-    op, om = _oracle_tree(orc, w).adjoint(w.r_s, w.rcut, 0.5, wt, s)
+    op, om, pa, ma = _oracle_tree(orc, w).adjoint(w.r_s, w.rcut, 0.5, wt, s, with_scale=True)
     assert np.abs(gp[s] - op).max() / np.abs(op).max() < 2e-5
     assert np.abs(gm[s] - om).max() / np.abs(om).max() < 2e-5
+    assert grad_scaled_err(gp[s], op, pa) < GRAD_TOL and grad_scaled_err(gm[s], om, ma) < GRAD_TOL
 
 
 def _scaled(w, L):
@@ -249,9 +251,11 @@ def test_non_power_of_two_box_adjoint(orc):
     dpos, dmass = m.shortrange_adjoint(tree, w.r_s, 0.5, torch.tensor(wt, dtype=torch.float32, device=dev))
     gp, gm = dpos.cpu().numpy(), dmass.cpu().numpy()
     s = np.arange(0, w.n, 7)
-    op, om = orc.Tree(w.pos, w.mass, 2.8 * w.eps, box=3.0).adjoint(w.r_s, w.rcut, 0.5, wt, s)
+    op, om, pa, ma = orc.Tree(w.pos, w.mass, 2.8 * w.eps, box=3.0).adjoint(w.r_s, w.rcut, 0.5, wt, s,
+                                                                          with_scale=True)
     assert np.abs(gp[s] - op).max() / np.abs(op).max() < 2e-5
     assert np.abs(gm[s] - om).max() / np.abs(om).max() < 2e-5
+    assert grad_scaled_err(gp[s], op, pa) < GRAD_TOL and grad_scaled_err(gm[s], om, ma) < GRAD_TOL
 
 
 def test_momentum_at_theta_zero():
@@ -290,3 +294,4 @@ def test_coincident_particles(orc):
     assert err_stats(a[100:], ao[100:])["rms"] <= 1e-5
     # the coincident ones feel only the background
     assert np.abs(a[:100] - ao[:100]).max() <= 1e-5 * np.abs(ao[:100]).max() + 1e-12
+

@@ -78,3 +78,42 @@ def test_two_body_gradient(orc):
     assert np.allclose(dp[1], -dp[0], rtol=1e-13)
     assert dm[1] == pytest.approx(float(wt[0] @ a[0]) / mass[1], rel=1e-13)
     assert dm[0] == pytest.approx(0.0, abs=1e-12)
+
+
+def test_adjoint_term_scale(orc):
+    """The term-magnitude sums bound the gradients (triangle inequality) and
+    equal them where one term of one sign makes up a component: two bodies
+    with the loss on body 0 only, so dL/dx_0 is a single target-side term and
+    dL/dm_1 the single source-side term w . g."""
+    w = ics.make("nfw256", 10)
+    T = orc.Tree(w.pos, w.mass, 2.8 * w.eps)
+    wt = ics.loss_weights(w.n, 98)
+    s = np.arange(0, w.n, 37)
+    dp, dm, pa, ma = T.adjoint(w.r_s, w.rcut, 0.5, wt, s, with_scale=True)
+    dp2, dm2 = T.adjoint(w.r_s, w.rcut, 0.5, wt, s)
+    assert np.array_equal(dp, dp2) and np.array_equal(dm, dm2)
+    assert np.all(np.abs(dp) <= pa * (1 + 1e-12)) and np.all(np.abs(dm) <= ma * (1 + 1e-12))
+    # many terms of both signs: the scale is well above the sum for most particles
+    assert np.median(ma / np.maximum(np.abs(dm), 1e-300)) > 2.0
+    pos = np.array([[0.5, 0.5, 0.5], [0.52, 0.51, 0.49]])
+    mass = np.array([1.0, 2.0])
+    T2 = orc.Tree(pos, mass, np.full(2, 0.003), leaf_size=1)
+    w2 = np.array([[0.3, -1.0, 2.0], [0.0, 0.0, 0.0]])
+    dp, dm, pa, ma = T2.adjoint(0.02, 0.09, 0.0, w2, with_scale=True)
+    assert np.allclose(pa[0], np.abs(dp[0]), rtol=1e-14)
+    assert ma[1] == pytest.approx(abs(dm[1]), rel=1e-14)
+
+
+def test_fd_crossing_flags(orc):
+    """A position step that moves a term across its softening length h sets
+    bit 0, across rcut bit 1; a pair well inside both sets neither."""
+    h, r_s = 0.004, 0.02
+    rcut = 4.5 * r_s
+    mass = np.array([1.0, 1.0])
+    cases = [(0.02, 0), (h - 2e-7, 1), (h + 2e-7, 1), (rcut - 2e-7, 2)]
+    for dx, want in cases:
+        pos = np.array([[0.5, 0.5, 0.5], [0.5 + dx, 0.5, 0.5]])
+        T = orc.Tree(pos, mass, np.full(2, h), leaf_size=1)
+        wt = np.array([[1.0, 0.5, 0.25], [0.0, 0.0, 0.0]])
+        _, _, fl = T.fd(r_s, rcut, 0.0, wt, np.array([0]), hx=1e-6, with_flags=True)
+        assert int(fl[0]) == want, (dx, int(fl[0]))
