@@ -7,9 +7,19 @@ og_shortrange_adjoint (FP32, frozen decisions).  value = interactions per
 step / step time.  The all-FP64 walk (the comparison variant) is timed on
 the same tree in the same run and reported under "fp64".
 
-Default workload: 128^3 Zel'dovich-displaced lattice (P(k) ~ k^-2, rms
-displacement 0.5 cells), eps = 1/3840, r_s = 1.25/256, rcut = 4.5 r_s,
-theta = 0.5.  L2 is flushed (256 MiB write) between timed steps.
+Default workload: the largest single-GPU set, 256^3 = 16,777,216 particles
+with 60% of the mass in 2000 NFW haloes and 40% uniform background,
+eps = 1/7680, r_s = 1.25/512, rcut = 4.5 r_s, theta = 0.5.  The 128^3
+Zel'dovich lattice and the 10.5M-particle zoom set are timed beside it.
+Inputs are larger than L2, which is flushed (256 MiB write) between timed
+steps anyway.
+
+Measured on the device in the same run: the FP32 (FFMA), packed FP32
+(FFMA2), special-function (MUFU) and FP64 (DFMA) pipe rates (og_probe_pipe),
+which the roofline fractions use beside the unit-count peak; and the error of
+the GPU walk against the FP64 oracle (tree at the same theta on the CPU
+baseline's sampled targets, direct sum on a bounded sample, theta = 0 on the
+4096-particle set).
 
 --impl reference times the CPU oracle (single-threaded FP64) on a bounded
 sample of the same workload.  Under torchrun (N > 1) every rank runs an
@@ -33,9 +43,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "short-range interactions/s and particles/s (fwd, fwd+adjoint) on 1 GB300, FP32 vs FP64"
 UNIT = "interactions/s"
-FWD_FLOPS = 51      # FP32 flops per forward interaction (FFMA = 2), counted from walk.cu
-ADJ_FLOPS = 75      # FP32 flops per adjoint interaction
-FWD_FP32_INSTR = 35  # FP32-pipe instructions per forward interaction (+2 MUFU)
+# FP32 flops per interaction (FFMA = 2).  "Algorithmic" is the canonical form
+# of one term: displacement 3, r^2 5, r 1, u 1, exp argument 2, erfcx
+# polynomial 20, f 3, m K f 4, accumulation 6 (plus 2 MUFU: rsqrt, ex2).  The
+# adjoint adds F'/r 6, d.w 5, (F'/r)(d.w) 1, J w 9, the target-side m J w 6 and
+# the source-side (J w, w.g) 4 after dropping the forward accumulation.
+# "Implemented" counts walk.cu as written (split-float displacement, degree-11
+# polynomial, Kahan fold).
+FWD_FLOPS = 45
+ADJ_FLOPS = 70
+FWD_FLOPS_IMPL = 51
+ADJ_FLOPS_IMPL = 75
+MUFU_PER_INTERACTION = 2
+FP64_FLOPS = 45      # the same canonical form in FP64 (CUDA's erfc / exp calls not counted)
 
 WORKLOADS = {
     "zeldovich128": "128^3 Zel'dovich lattice, P(k)~k^-2, rms disp 0.5 cells, eps=1/3840, r_s=1.25/256, theta=0.5",
@@ -77,11 +97,11 @@ def job_rate(units_per_rank: float, ws: int, ms: float) -> float:
     return ws * units_per_rank / (ms * 1e-3)
 
 
-def walk_traffic(kernel: str, summary="walk_fp32_zeldovich128.md"):
-    """DRAM bytes per launch of a walk kernel ("forward" or "adjoint") from
-    the committed ncu summary, if it was taken on the current walk.cu (else
-    None)."""
-    path = os.path.join(ROOT, "profiles", summary)
+def walk_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of a walk kernel ("forward" or "adjoint") on this
+    workload from the committed ncu summary, if it was taken on the current
+    walk.cu (else None)."""
+    path = os.path.join(ROOT, "profiles", f"walk_fp32_{workload}.md")
     src = os.path.join(ROOT, "paper_2606_17145_gb300", "csrc", "walk.cu")
     try:
         text = open(path).read()
@@ -150,31 +170,112 @@ class Clocks:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
+def host_info():
+    """Host core count and CPU model (lscpu), for the CPU baseline."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                             timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"host_cores": os.cpu_count(), "cpu_model": model}
+
+
+def pipe_peaks(og, L, dev):
+    """Measured pipe rates (og_probe_pipe, CUDA events, best of 3 launches)."""
+    import ctypes as C
+    import torch
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    out = {}
+    for kind, name, iters in ((0, "ffma", 4096), (1, "ffma2", 2048), (2, "mufu", 1024), (3, "dfma", 256)):
+        ops = C.c_uint64()
+        best = None
+        for _ in range(4):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            code = L.og_probe_pipe(kind, iters, C.c_void_p(sink.data_ptr()), C.byref(ops),
+                                   C.c_void_p(torch.cuda.current_stream().cuda_stream))
+            b.record()
+            torch.cuda.synchronize()
+            if code != 0:
+                raise SystemExit(f"og_probe_pipe({name}) failed: {code}")
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        out[name] = ops.value / (best * 1e-3)   # operations per second
+    return {"fp32_tflops": 2 * out["ffma"] / 1e12, "fp32x2_tflops": 2 * out["ffma2"] / 1e12,
+            "mufu_per_s": out["mufu"], "fp64_tflops": 2 * out["dfma"] / 1e12,
+            "how": "og_probe_pipe: independent FMA / f32x2 FMA / rsqrt+ex2 / DFMA chains, 4 blocks x 256 "
+                   "threads per SM, best of 4 launches timed with CUDA events"}
+
+
 # ----------------------------------------------------------------- CPU oracle
 
-def oracle_throughput(w, theta, budget_s=12.0, min_targets=4096, seed=5):
+def oracle_throughput(w, theta, budget_s=12.0, min_targets=1024, seed=5, T=None):
     """Single-threaded FP64 oracle forward walk on sampled targets (tree built
-    once, untimed).  Returns (interactions/s, particles/s, sample text)."""
+    once, untimed).  Returns (interactions/s, particles/s, sample text,
+    targets, oracle accelerations of those targets)."""
     import numpy as np
     import oracle
     t0 = time.time()
-    T = oracle.Tree(w.pos, w.mass, 2.8 * w.eps)
+    own = T is None
+    if own:
+        T = oracle.Tree(w.pos, w.mass, 2.8 * w.eps)
     build_s = time.time() - t0
     rng = np.random.default_rng(seed)
     perm = rng.permutation(w.n)
     done, inter, spent = 0, 0, 0.0
     chunk = min_targets
+    accs = []
     while done < w.n and (spent < budget_s or done < min_targets):
         tg = perm[done:done + chunk]
         t1 = time.time()
-        _, cnt = T.walk(w.r_s, w.rcut, theta, tg)
+        a, cnt = T.walk(w.r_s, w.rcut, theta, tg)
         spent += time.time() - t1
+        accs.append(a)
         inter += int(cnt.sum())
         done += len(tg)
-    T.close()
+    if own:
+        T.close()
     sample = (f"oracle tree walk (1 thread, FP64, -O2) of {done} random targets of the {w.n}-particle set "
               f"(tree over all particles built once, {build_s:.1f} s, untimed); forward walk only")
-    return inter / spent, done / spent, sample, done, spent
+    return inter / spent, done / spent, sample, perm[:done], np.concatenate(accs)
+
+
+def rel_stats(a, ref):
+    """Per-particle relative error |a_i - ref_i| / |ref_i|: rms, median, p99, max."""
+    import numpy as np
+    r = np.linalg.norm(a - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+    return {"rms": float(np.sqrt(np.mean(r * r))), "median": float(np.median(r)),
+            "p99": float(np.percentile(r, 99)), "max": float(r.max()), "n": int(len(r))}
+
+
+def accuracy_c1(og, dev):
+    """GPU FP32 walk on the 4096-particle uniform set against the oracle direct
+    sum: rms at theta = 0 and p99 for a range of theta."""
+    import numpy as np
+    import ics
+    import oracle
+    import torch
+    w = ics.make("uniform4096")
+    pos = torch.tensor(w.pos, device=dev)
+    mass = torch.tensor(w.mass, device=dev)
+    eps = torch.tensor(w.eps, device=dev)
+    k, o = og.keys_sort(pos, w.box)
+    tree = og.tree_build(k, o, pos, mass, eps, w.box)
+    ad, _ = oracle.direct(w.pos, w.mass, 2.8 * w.eps, w.box, w.r_s, w.rcut)
+    out = {}
+    for th in (0.0, 0.2, 0.3, 0.5):
+        a, _, _ = og.shortrange_accel(tree, w.r_s, th)
+        out[f"theta_{th}"] = rel_stats(a.double().cpu().numpy(), ad)
+    ok = [th for th in (0.5, 0.3, 0.2) if out[f"theta_{th}"]["p99"] <= 5e-3]
+    return {"set": "uniform4096 (4096 uniform, eps=1/480, r_s=1.25/16) vs oracle direct sum",
+            "theta0_rms": out["theta_0.0"]["rms"], "p99_by_theta": {k: v["p99"] for k, v in out.items()},
+            "largest_theta_with_p99_le_5e-3": max(ok) if ok else None}
 
 
 def run_reference(args, w, ws, rank):
@@ -203,7 +304,7 @@ def run_reference(args, w, ws, rank):
                        "step": f"oracle forward walk of {per_step} random targets"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{per_step} random targets per step, tree over all {w.n} particles "
-                                       "built once (untimed); forward walk only"},
+                                       "built once (untimed); forward walk only", **host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -211,21 +312,80 @@ def run_reference(args, w, ws, rank):
 
 # ----------------------------------------------------------------- GPU arm
 
+def timed_ms(fn, reps, flush, warm=0):
+    """Mean CUDA-event time of fn over reps calls (L2 flushed before each)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return sum(ts) / len(ts)
+
+
+def side_workload(og, L, name, dev, theta, steps, flush):
+    """Keys, tree, FP32 forward and adjoint walks on another workload (stream
+    launches, L2 flushed): per-phase times and rates."""
+    import ctypes as C
+    import ics
+    import torch
+    w = ics.make(name)
+    pos = torch.tensor(w.pos, device=dev)
+    mass = torch.tensor(w.mass, device=dev)
+    eps = torch.tensor(w.eps, device=dev)
+    wt = torch.tensor(ics.loss_weights(w.n, 2002), dtype=torch.float32, device=dev)
+    wsk = og._workspace(L.og_keys_sort_ws_bytes(w.n), dev)
+    k, o = og.keys_sort(pos, w.box, ws=wsk)
+    tree = og.tree_build(k, o, pos, mass, eps, w.box)
+    ws = og._workspace(L.og_accel_ws_bytes(C.byref(tree.header), 0), dev)
+    wsa = og._workspace(L.og_adjoint_ws_bytes(C.byref(tree.header), 1), dev)
+    acc = torch.empty((w.n, 3), dtype=torch.float32, device=dev)
+    tot = torch.zeros(1, dtype=torch.int64, device=dev)
+    og.shortrange_accel(tree, w.r_s, theta, ws=ws, out=acc, total=tot)
+    og.shortrange_adjoint(tree, w.r_s, theta, wt, ws=wsa)
+    inter = int(tot.item())
+    t_keys = timed_ms(lambda: og.keys_sort(pos, w.box, check=False, ws=wsk, keys=k, order=o), steps, flush)
+    t_tree = timed_ms(lambda: og.tree_build(k, o, pos, mass, eps, w.box, check=False, mem=tree.mem), steps, flush)
+    t_fwd = timed_ms(lambda: og.shortrange_accel(tree, w.r_s, theta, check=False, ws=ws, out=acc, total=tot),
+                     steps, flush)
+    t_adj = timed_ms(lambda: og.shortrange_adjoint(tree, w.r_s, theta, wt, check=False, ws=wsa), steps, flush)
+    step = t_keys + t_tree + t_fwd + t_adj
+    return {"workload": f"{name}: {WORKLOADS[name]}", "n": w.n, "interactions_per_step": inter,
+            "ms": {"keys_sort": t_keys, "tree_build": t_tree, "accel_fp32": t_fwd, "adjoint_fp32": t_adj,
+                   "step": step},
+            "interactions_per_s": inter / (step * 1e-3), "fwd_interactions_per_s": inter / (t_fwd * 1e-3),
+            "adj_interactions_per_s": inter / (t_adj * 1e-3), "fwd_particles_per_s": w.n / (t_fwd * 1e-3),
+            "timed_steps": steps, "launch": "stream launches, L2 flushed"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="zeldovich128", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="nfw256", choices=sorted(WORKLOADS))
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-targets", type=int, default=8192)
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--ref-targets", type=int, default=None,
+                    help="oracle targets per reference-arm step (default: 1024, or 8192 for zeldovich128)")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--side", default="zeldovich128,zoom8m",
+                    help="other workloads timed beside the line (comma list, empty for none)")
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel instead of replaying a CUDA graph")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.ref_targets is None:
+        args.ref_targets = 8192 if args.workload == "zeldovich128" else 1024
     ws, rank, local = dist_env()
 
     import numpy as np
@@ -272,7 +432,8 @@ def main():
     dpos = torch.empty((n, 3), dtype=torch.float64, device=dev)
     dmass = torch.empty(n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
+
+    peaks = pipe_peaks(og, L, dev)
 
     state = {}
 
@@ -356,7 +517,7 @@ def main():
         torch.cuda.synchronize()
         wall = time.time() - t_wall
     # per-phase breakdown (separately launched steps with events between phases)
-    for _ in range(min(args.steps, 10)):
+    for _ in range(min(args.steps, 3)):
         flush.zero_()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         ev[0].record()
@@ -372,10 +533,8 @@ def main():
 
     # FP64 walk on the same tree (comparison variant)
     tr = state["tree"]
-    og.shortrange_accel(tr, w.r_s, args.theta, prec="fp64", check=False, ws=ws_acc, out=acc64, total=total64)
-    torch.cuda.synchronize()
     f64 = []
-    for _ in range(args.fp64_steps):
+    for _ in range(max(1, args.fp64_steps)):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -389,8 +548,11 @@ def main():
     code = og.poll_status(ws_acc)
     if code != 0:
         raise SystemExit(f"fp64 walk failed on the device: {L.og_status_str(code).decode()}")
+    # the FP32 accelerations of the same tree (the graph's last replay wrote acc)
+    og.shortrange_accel(tr, w.r_s, args.theta, ws=ws_acc, out=acc, total=total)
     rel = (acc.double() - acc64).norm(dim=1) / acc64.norm(dim=1).clamp_min(1e-300)
     fp32_vs_fp64 = {"rms_rel": float(rel.pow(2).mean().sqrt()), "max_rel": float(rel.max())}
+    acc_host = acc.double().cpu().numpy()
 
     # end to end through the public API with host buffers
     pos_h = pos.cpu().pin_memory()
@@ -447,7 +609,8 @@ def main():
     e2e_step()
     torch.cuda.synchronize()
     e2e_ms = []
-    for _ in range(args.steps):
+    e2e_steps = min(args.steps, 5)
+    for _ in range(e2e_steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -458,20 +621,36 @@ def main():
         e2e_ms.append(a.elapsed_time(b))
     e2e_mean = max_over_ranks(sum(e2e_ms) / len(e2e_ms), ws, dev)
 
-    # roofline of the dominant kernel (FP32 ALU bound; peak from unit counts and the max SM clock)
-    peaks = measured_peaks()
+    # roofline of the dominant kernel.  "peak" is the unit-count FP32 peak
+    # (SMs x 128 FMA lanes x 2 flops x the maximum SM clock); the pipe rates
+    # measured above give the "_measured" fractions and the MUFU and FP64 ones.
+    mp = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FP32 FMA lanes x 2 x clock
-    walk = {"accel_fp32": (pms["accel_fp32"], FWD_FLOPS), "adjoint_fp32": (pms["adjoint_fp32"], ADJ_FLOPS)}
-    dom = max(walk, key=lambda k: walk[k][0])
-    dom_ms, dom_flops = walk[dom]
-    achieved = interactions * dom_flops / (dom_ms * 1e-3) / 1e12
-    traffic = walk_traffic("forward" if dom == "accel_fp32" else "adjoint")
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": traffic, "kernel": dom,
-                "flops_per_interaction": dom_flops,
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz (max SM clock)"}
+    sm_max = float(mp.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    kern = {}
+    for kname, kms, fl, fli in (("accel_fp32", pms["accel_fp32"], FWD_FLOPS, FWD_FLOPS_IMPL),
+                                ("adjoint_fp32", pms["adjoint_fp32"], ADJ_FLOPS, ADJ_FLOPS_IMPL)):
+        rate = interactions / (kms * 1e-3)
+        tf = rate * fl / 1e12
+        kern[kname] = {"ms": kms, "interactions_per_s": rate, "tflops_algorithmic": tf,
+                       "tflops_implemented": rate * fli / 1e12, "frac_fp32": tf / alu_peak,
+                       "frac_fp32_measured": tf / peaks["fp32_tflops"],
+                       "mufu_per_s": rate * MUFU_PER_INTERACTION,
+                       "frac_xu": rate * MUFU_PER_INTERACTION / peaks["mufu_per_s"]}
+    r64 = inter64 / (f64_ms * 1e-3)
+    kern["accel_fp64"] = {"ms": f64_ms, "interactions_per_s": r64, "tflops_algorithmic": r64 * FP64_FLOPS / 1e12,
+                          "frac_fp64_measured": r64 * FP64_FLOPS / 1e12 / peaks["fp64_tflops"]}
+    dom = max(("accel_fp32", "adjoint_fp32"), key=lambda k: kern[k]["ms"])
+    dk = kern[dom]
+    traffic = walk_traffic("forward" if dom == "accel_fp32" else "adjoint", args.workload)
+    roofline = {"bound": "alu", "achieved": dk["tflops_algorithmic"], "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": dk["tflops_algorithmic"] / alu_peak, "traffic": traffic, "kernel": dom,
+                "flops_per_interaction": ADJ_FLOPS if dom == "adjoint_fp32" else FWD_FLOPS,
+                "flops_per_interaction_implemented": ADJ_FLOPS_IMPL if dom == "adjoint_fp32" else FWD_FLOPS_IMPL,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz (max SM clock)",
+                "frac_measured": dk["frac_fp32_measured"], "frac_xu": dk["frac_xu"],
+                "measured_peaks": peaks, "kernels": kern}
 
     launches = og.LAUNCHES_PER_CALL
     per_step_launches = (launches["keys_sort"] + launches["tree_build"] + launches["accel"] +
@@ -485,20 +664,11 @@ def main():
     ws_pm = og._workspace(plan.ws_bytes, dev)
     acc_pm = torch.empty((n, 3), dtype=torch.float32, device=dev)
     og.pm_accel(plan, pos, mass, w.box, w.r_s, ws=ws_pm, out=acc_pm)  # checked once
-    for _ in range(args.warmup):
-        og.pm_accel(plan, pos, mass, w.box, w.r_s, check=False, ws=ws_pm, out=acc_pm)
-    pm_times = []
-    for _ in range(max(1, min(args.steps, 20))):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        og.pm_accel(plan, pos, mass, w.box, w.r_s, check=False, ws=ws_pm, out=acc_pm)
-        e1.record()
-        torch.cuda.synchronize()
-        pm_times.append(e0.elapsed_time(e1))
-    pm_ms = max_over_ranks(sum(pm_times) / len(pm_times), ws, dev)
+    pm_local = timed_ms(lambda: og.pm_accel(plan, pos, mass, w.box, w.r_s, check=False, ws=ws_pm, out=acc_pm),
+                        max(1, min(args.steps, 10)), flush, warm=args.warmup)
+    pm_ms = max_over_ranks(pm_local, ws, dev)
     plan.close()
+    del ws_pm, acc_pm
 
     # one device-resident kick-drift-kick step (kick, drift, keys, tree, FP32
     # walk, PM mesh, kick) on copies of the inputs; reported beside the line,
@@ -507,21 +677,10 @@ def main():
     try:
         vel0 = torch.zeros_like(pos)
         S = og.TreePMStepper(pos.clone(), vel0, mass, eps, w.box, w.r_s, args.theta, pm_n)
-        dt_k = 1e-4
-        for _ in range(args.warmup):
-            S.step(dt_k)
-        kt = []
-        for _ in range(max(1, min(args.steps, 10))):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            S.step(dt_k)
-            e1.record()
-            torch.cuda.synchronize()
-            kt.append(e0.elapsed_time(e1))
+        kdk_local = timed_ms(lambda: S.step(1e-4, check=False), max(1, min(args.steps, 3)), flush, warm=1)
+        S.poll()
         S.close()
-        kdk_local = sum(kt) / len(kt)
+        del S, vel0
     except Exception as e:  # the headline line must still be printed
         kdk_local, kdk = float("inf"), {"error": f"{type(e).__name__}: {e}"}
     # every rank takes part in the max, whether or not its leg failed
@@ -532,30 +691,18 @@ def main():
                         "stream launches (no graph), L2 flushed"}
                if kdk_ms < float("inf") else {"error": "failed on another rank"})
 
-    # SPH density and smoothing length on the same tree (first version: one
-    # thread per particle, FP64), reported beside the line
+    # SPH density and smoothing length on the same tree, reported beside the line
     sph = None
     try:
         n_ngb = 32.0
         og.sph_density(tree, n_ngb)  # warm-up, checked
-        st = []
-        for _ in range(2):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            og.sph_density(tree, n_ngb, check=False)
-            e1.record()
-            torch.cuda.synchronize()
-            st.append(e0.elapsed_time(e1))
-        sph_local = sum(st) / len(st)
+        sph_local = timed_ms(lambda: og.sph_density(tree, n_ngb, check=False), 1, flush)
     except Exception as e:  # the headline line must still be printed
         sph_local, sph = float("inf"), {"error": f"{type(e).__name__}: {e}"}
     sph_ms = max_over_ranks(sph_local, ws, dev)
     if sph is None:
-        sph = ({"ms": sph_ms, "particles_per_s": ws * n / (sph_ms * 1e-3), "n_ngb": 32.0,
-                "what": "og_sph_density: per-particle tree gather, bisection of h, density; FP64, one thread "
-                        "per particle"}
+        sph = ({"ms": sph_ms, "particles_per_s": ws * n / (sph_ms * 1e-3), "n_ngb": n_ngb,
+                "what": "og_sph_density: tree gather, smoothing length by bisection, density"}
                if sph_ms < float("inf") else {"error": "failed on another rank"})
 
     line = {
@@ -564,17 +711,20 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": n, "theta": args.theta,
                    "step": "keys_sort + tree_build + accel_fp32 + adjoint_fp32 (inputs resident)",
-                   "l2": "flushed by a 256 MiB write between timed steps", "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2; also flushed by a 256 MiB write between timed steps",
+                   "parallelism": f"replicas x{ws}",
                    "launch": "CUDA graph replay of the whole step" if graph is not None else "stream launches"},
         "clocks": clocks,
         "e2e": {"value": job_rate(interactions, ws, e2e_mean), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean, "steps": e2e_steps},
         "gpu_launches": per_step_launches * args.steps,
         "roofline": roofline,
         "interactions_per_step": interactions,
         "particles_per_s": ws * n / (ms * 1e-3),
         "fwd_interactions_per_s": ws * interactions / (pms["accel_fp32"] * 1e-3),
         "fwd_particles_per_s": ws * n / (pms["accel_fp32"] * 1e-3),
+        "adj_interactions_per_s": ws * interactions / (pms["adjoint_fp32"] * 1e-3),
+        "fwd_adj_particles_per_s": ws * n / ((pms["accel_fp32"] + pms["adjoint_fp32"]) * 1e-3),
         "breakdown_ms": pms,
         "fp64": {"ms": f64_ms, "interactions_per_s": ws * inter64 / (f64_ms * 1e-3),
                  "same_interactions": inter64 == interactions,
@@ -586,10 +736,47 @@ def main():
                "what": "og_pm_accel: CIC deposit, cuFFT R2C, Green's function, cuFFT C2R, "
                        "difference + interpolation; FP32 mesh; timed apart from the step, L2 flushed"},
     }
+    del ws_adj, dpos, dmass, acc64
+    torch.cuda.empty_cache()
+
+    # other workloads, timed beside the line
+    side = {}
+    for name in [x for x in args.side.split(",") if x]:
+        if name == args.workload or name not in WORKLOADS:
+            continue
+        try:
+            side[name] = side_workload(og, L, name, dev, args.theta, 1 if name == "zoom8m" else 5, flush)
+        except Exception as e:
+            side[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
+    line["other_workloads"] = side
+
     if rank == 0 and not args.no_cpu_baseline:
-        v, pps, sample, done, spent = oracle_throughput(w, args.theta)
+        import oracle
+        oracle.build()
+        t0 = time.time()
+        T = oracle.Tree(w.pos, w.mass, 2.8 * w.eps)
+        v, pps, sample, tg, a_or = oracle_throughput(w, args.theta, T=T)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-                                "particles_per_s": pps}
+                                "particles_per_s": pps, **host_info()}
+        # error against the FP64 oracle: the tree at the same theta on the
+        # sampled targets, the direct sum on a time-bounded subset of them
+        acc_or = {"vs_oracle_tree": rel_stats(acc_host[tg], a_or)}
+        dt_, done, ad_l = 0.0, 0, []
+        while done < len(tg) and (dt_ < 8.0 or done < 256):
+            t1 = time.time()
+            ad, _ = oracle.direct(w.pos, w.mass, 2.8 * w.eps, w.box, w.r_s, w.rcut, tg[done:done + 64])
+            dt_ += time.time() - t1
+            ad_l.append(ad)
+            done += 64
+        acc_or["vs_oracle_direct"] = rel_stats(acc_host[tg[:done]], np.concatenate(ad_l))
+        acc_or["oracle_tree_vs_direct"] = rel_stats(a_or[:done], np.concatenate(ad_l))
+        acc_or["c1"] = accuracy_c1(og, dev)
+        acc_or["how"] = (f"per-particle |a_gpu - a_ref| / |a_ref| of the FP32 walk at theta = {args.theta}; "
+                         "vs_oracle_tree on the CPU baseline's sampled targets, vs_oracle_direct on the first "
+                         "of them (the direct sum's time bound), c1 on the 4096-particle uniform set")
+        line["accuracy"] = acc_or
+        T.close()
     if ws > 1:
         torch.distributed.barrier(device_ids=[local])
     if rank == 0:

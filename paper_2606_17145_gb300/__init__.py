@@ -338,12 +338,25 @@ class TreePMStepper:
         pm_accel(self.plan, self.pos, self.mass, self.box, self.r_s, stream=stream, check=check, ws=self.ws_pm,
                  out=self.acc_l)
 
-    def step(self, dt: float, check: bool = False, stream=None):
-        """One kick-drift-kick step of length dt."""
+    def poll(self, stream=None):
+        """Synchronise and raise OGError if keys, tree, walk or mesh recorded
+        an error on the device since their last call."""
+        for buf, where in ((self.ws_keys, "og_keys_sort"), (self.tree_mem, "og_tree_build"),
+                           (self.ws_acc, "og_shortrange_accel"), (self.ws_pm, "og_pm_accel")):
+            if buf is not None:
+                _check(poll_status(buf, stream), f"{where} (device, stepper)")
+
+    def step(self, dt: float, check: bool = True, stream=None):
+        """One kick-drift-kick step of length dt.  With check (the default) the
+        device status words are read once, after the second kick (one
+        synchronisation per step); a failed tree makes the walk return NaN
+        forces, so an unchecked step cannot silently reuse old ones."""
         kick(self.vel, self.acc_s, self.acc_l, 0.5 * dt, stream)
         drift(self.pos, self.vel, dt, stream)
-        self.forces(check=check, stream=stream)
+        self.forces(check=False, stream=stream)
         kick(self.vel, self.acc_s, self.acc_l, 0.5 * dt, stream)
+        if check:
+            self.poll(stream)
 
     def close(self):
         self.plan.close()

@@ -936,7 +936,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   const int64_t g = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
   if (g >= T.ngroups) return;
   if (T.sb->status != 0 || T.sb->magic != kMagicTree) {
+    // a failed or missing tree: flag it and give every output NaN (each
+    // index k < n is written by exactly one lane; no permutation is read),
+    // so that nothing downstream can take stale values for forces
     if (lane == 0) set_status(A.wsb, ST_NOTREE);
+    const int64_t kk = g * kGroup + lane;
+    if (kk < T.n) {
+      const float nf = __int_as_float(0x7fc00000);
+      const double nd = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (A.accf) A.accf[3 * kk + c] = nf;
+        if (A.accd) A.accd[3 * kk + c] = nd;
+        if (A.tgt) A.tgt[3 * kk + c] = nd;
+      }
+      if (A.counts) A.counts[kk] = -1;
+    }
     return;
   }
   WarpBufs W;

@@ -88,3 +88,25 @@ def test_binary_returns_after_one_kepler_period():
     err = np.linalg.norm(S.pos.cpu().numpy() - pos, axis=1).max() / r0
     S.close()
     assert err < 1.5e-3, err
+
+
+def test_stepper_reports_a_failed_tree():
+    """A step whose tree build runs out of node capacity raises (the status
+    words are polled once per step), and an unchecked step leaves NaN
+    short-range forces rather than the previous step's."""
+    import numpy as np
+    from gpu_util import device, og, to_dev
+    import ics
+    dev = device()
+    m = og()
+    w = ics.make("uniform4096", 2000)
+    pos, mass, eps = to_dev(w, dev)
+    S = m.TreePMStepper(pos.clone(), torch.zeros_like(pos), mass, eps, w.box, w.r_s, 0.5, 16)
+    S.step(1e-4)                         # a clean step polls without error
+    S.p = m.params(node_capacity=40)     # the same buffer, too few nodes allowed
+    with pytest.raises(m.OGError) as e:
+        S.step(1e-4)
+    assert e.value.code == 2             # OG_ENOSPACE from the tree build
+    S.step(1e-4, check=False)
+    assert torch.isnan(S.acc_s).all()
+    S.close()
