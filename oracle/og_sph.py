@@ -1,7 +1,8 @@
 """FP64 CPU oracle for the SPH density / smoothing-length iteration.
 
-TEST INFRASTRUCTURE ONLY: the slow, obviously-correct reference for a
-future device implementation of the density walk.  Only the tests use it.
+TEST INFRASTRUCTURE ONLY: the slow, obviously-correct reference that the
+device's grouped density walk (og_sph_density) is compared with.  Only the
+tests and the benchmark's CPU legs use it.
 
 The paper's SPH density module iterates the smoothing length of each
 particle until its sphere holds a fixed number of neighbours, and its

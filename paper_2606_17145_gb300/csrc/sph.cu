@@ -2,164 +2,516 @@
 // include/og.h: og_sph_ws_bytes / og_sph_density).
 //
 // The paper's SPH density module iterates each particle's smoothing length
-// until its sphere holds a fixed number of neighbours, and gathers the
-// neighbours inside a sphere before evaluating them (Sec. 2.1).  The reading
-// is GADGET-2's: W is the cubic spline with support h,
-// rho_i = sum_j m_j W(r_ij, h_i) (the particle itself included), and h_i is
-// the root of the kernel-weighted count
+// until its sphere holds a fixed number of neighbours, gathering the
+// neighbours inside a sphere before evaluating them; its walks group nearby
+// targets (Sec. 2, 2.1).  The reading is GADGET-2's: W is the cubic spline
+// with support h, rho_i = sum_j m_j W(r_ij, h_i) (the particle itself
+// included), and h_i is the root of the kernel-weighted count
 // N_eff(h) = (4 pi / 3) h^3 sum_j W(r_ij, h) = (32 / 3) sum_j w(r_ij / h) = N_ngb.
 //
-// First version, written for correctness on the existing keys and tree: one
-// thread per particle, FP64 distances in box units with the periodic minimum
-// image.  A thread gathers every particle within a search radius H from a
-// stack walk of the tree (cube-sphere test), widens H until N_eff(H) >= N_ngb
-// or narrows it when the gather overflows its list, then bisects h in [0, H]
-// over the gathered distances: w(r / h) = 0 for r >= h, so for h <= H the
-// gathered set gives the full sum.  Every loop and buffer is bounded; an
-// overflow or a failed bracket sets a status bit and writes NaN.
+// Grouped walk.  One warp serves a group of 32 Hilbert-consecutive targets
+// (lane = target), as in the gravity walk.  Each pass gathers, from one
+// traversal of the tree, every leaf whose cube comes within the largest
+// lane radius of the group's bounding box (a range stack popped 32 nodes at a
+// time), and every lane evaluates the gathered particles against its own
+// radius.
+//   1. Start: the density of the smallest ancestor of the target's leaf that
+//      holds at least N_ngb particles gives h = (3 N_ngb / 4 pi n)^(1/3).
+//   2. FP32 passes: Newton steps on ln h, ln N_eff(h) = ln N_ngb, with
+//      d ln N_eff / d ln h = -sum q w'(q) / sum w(q), a bracket of the root kept
+//      from every evaluation (a step leaving it is replaced by the bracket's
+//      geometric mean) and steps clamped to a factor 2; until |d ln h| < 1e-5.
+//      Distances come from the split-float positions (FP64 accuracy rounded
+//      to FP32).
+//   3. FP64 pass: each lane lists its candidates within h (1 + 4e-6) (FP32
+//      test with a margin) in shared memory, and the lists are evaluated
+//      lane-parallel in FP64 (the FP64 pipe is too narrow for lane-masked
+//      evaluation of every group candidate).  One Newton step from the FP32
+//      root gives h; the density at that h follows to first order from the
+//      sums at the evaluated h (the step is below 3e-6 h, so the neglected
+//      term is ~1e-11 relative); the neighbour count at the new h is the
+//      count at the evaluated one corrected by the neighbours within 4e-6 h
+//      of it (their distances are kept, up to two; with more the pass is
+//      repeated at the new h).
+// Every loop is bounded (node-visit cap, pass caps, the stack bound); a
+// particle whose h does not converge below half the box gets NaN / -1 and
+// sets a status bit.
 #include <cmath>
 
 #include "og_internal.cuh"
 
 namespace og {
 
-constexpr int kSphList = 256;   // gathered neighbours per particle
-constexpr int kSphStack = 8 * (kLevels + 1);  // at most 8 children pushed per level
-constexpr int kSphTries = 24;   // search-radius changes
-constexpr int kSphBisect = 64;  // bisection steps (2^-64 of the bracket)
-
-__device__ __forceinline__ double sph_w(double q) {
-  if (q <= 0.5) return 1.0 - 6.0 * q * q + 6.0 * q * q * q;
-  if (q <= 1.0) {
-    const double t = 1.0 - q;
-    return 2.0 * t * t * t;
-  }
-  return 0.0;
-}
-
-__device__ __forceinline__ double sph_mi(double t) { return t - rint(t); }
+constexpr int kSphWarps = 2;          // warps per block
+constexpr int kSphStack = 276;        // range stack entries (same bound as the gravity walk)
+constexpr int kSphStackNeed = 32;     // pushes of one step
+constexpr int kSphDeep = 64;          // above this depth a step pops a single range
+static_assert(kSphDeep + 31 + 7 * 20 + 8 <= kSphStack - kSphStackNeed, "stack bound");
+constexpr int kSphQueue = 128;        // queued leaves per warp
+constexpr int kSphQueueNeed = 32;     // a step queues at most one leaf per popped node
+constexpr int kSphList = 32;          // FP64 pass: listed candidates per lane before a flush
+constexpr int kSphPass32 = 24;        // FP32 Newton passes at most
+constexpr int kSphPass64 = 4;         // FP64 passes at most
 
 struct SphArgs {
   TreeDev T;
   StatusBlock* wsb;
   BoxScale B;
   double n_ngb;
-  double h0;  // first search radius, box units
+  long long max_visits;  // node visits per gather
   double* h_out;
   double* rho_out;
   int32_t* ngb_out;
 };
 
-// Gather the particles within H (box units) of x into (r, j); returns the
-// number found, which exceeds kSphList on overflow (the list then holds the
-// first kSphList), or -1 on a corrupt link or a stack overflow.
-__device__ int sph_gather(const SphArgs& A, const double x[3], double H, double* r, int* jl) {
+// Minimum image of a box-unit difference t (|t| < 1.5): t - rint(t).
+__device__ __forceinline__ float sph_mi1(float t) {
+  const float r = __fadd_rn(__fadd_rn(t, 12582912.0f), -12582912.0f);
+  return __fadd_rn(t, -r);
+}
+
+// w(q) and q w'(q) of the cubic spline (w = 1 - 6 q^2 + 6 q^3 for q <= 1/2,
+// 2 (1 - q)^3 for 1/2 < q < 1, 0 beyond).
+__device__ __forceinline__ void spline_w32(float q, float& w, float& wq) {
+  if (q <= 0.5f) {
+    const float q2 = q * q;
+    w = fmaf(q2, 6.0f * q - 6.0f, 1.0f);
+    wq = q2 * (18.0f * q - 12.0f);
+  } else if (q < 1.0f) {
+    const float t = 1.0f - q;
+    w = 2.0f * t * t * t;
+    wq = -6.0f * q * t * t;
+  } else {
+    w = 0.0f;
+    wq = 0.0f;
+  }
+}
+__device__ __forceinline__ void spline_w64(double q, double& w, double& wq) {
+  if (q <= 0.5) {
+    const double q2 = q * q;
+    w = fma(q2, 6.0 * q - 6.0, 1.0);
+    wq = q2 * (18.0 * q - 12.0);
+  } else if (q < 1.0) {
+    const double t = 1.0 - q;
+    w = 2.0 * t * t * t;
+    wq = -6.0 * q * t * t;
+  } else {
+    w = 0.0;
+    wq = 0.0;
+  }
+}
+
+struct SphBufs {
+  int* stack;
+  int2* queue;
+  int* qoff;        // [kSphQueue + 1] slot offsets of the queued leaves
+  float4* sa;       // [32] staged candidates: hi part
+  float4* sb;       // [32] lo part
+  int* sj;          // [32] sorted index
+  int (*list)[32];  // [kSphList][lane]
+};
+
+struct SphGroup {
+  float cx, cy, cz, ex, ey, ez;  // group box centre and half extents (box units, padded)
+};
+
+// One gather: every leaf whose cube comes within R (box units) of the group
+// box is passed to eval(first, count), in batches.  Warp-uniform control
+// flow.  Returns status bits (0 if clean).
+template <class Eval>
+__device__ uint32_t sph_gather(const SphArgs& A, const SphBufs& W, const SphGroup& G, float R, int nodes_total,
+                               int lane, Eval& eval) {
   const TreeDev& T = A.T;
-  int stack[kSphStack];
-  int sp = 0, found = 0;
-  stack[sp++] = 0;  // the root
-  while (sp > 0) {
-    const int p = stack[--sp];
-    if (p < 0 || p >= T.cap) return -1;
-    const int4 D = T.nD[p];
-    const float4 NC = T.nC[p];
-    const double hs = 0.5 * (double)NC.w;
-    double d2 = 0.0;
-    const double c[3] = {(double)NC.x, (double)NC.y, (double)NC.z};
+  const float R2 = (R * 1.00001f + 1e-7f) * (R * 1.00001f + 1e-7f);
+  const uint32_t lt = (1u << lane) - 1u;
+  if (lane == 0) W.stack[0] = (int)(1u << 28);  // the root: node 0, one node
+  int sp = 1, nq = 0;
+  long long visits = 0;
+  __syncwarp();
+  for (;;) {
+    if (sp > 0 && nq <= kSphQueue - kSphQueueNeed) {
+      if (sp > kSphStack - kSphStackNeed) return ST_STACK;
+      const int m = sp > kSphDeep ? 1 : min(sp, 32);
+      const uint32_t E = (uint32_t)W.stack[max(sp - 1 - lane, 0)];
+      __syncwarp();
+      const int rcnt = lane < m ? (int)(E >> 28) : 0;
+      const int rfirst_l = (int)(E & 0x0fffffffu);
+      if (__any_sync(0xffffffffu, lane < m && (rcnt < 1 || rcnt > 8))) return ST_TREELINK;
+      int incl = rcnt;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double g = fabs(sph_mi(x[a] - c[a])) - hs;
-      if (g > 0.0) d2 += g * g;
-    }
-    if (d2 >= H * H) continue;  // the cube lies beyond the sphere
-    if (meta_leaf(D.w)) {
-      for (int j = D.x; j < D.x + D.y; ++j) {
-        if (j < 0 || j >= T.n) return -1;
-        double s2 = 0.0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const double t = sph_mi(x[a] - div_box(T.x64[3 * (int64_t)j + a], A.B));
-          s2 += t * t;
-        }
-        const double rr = sqrt(s2);
-        if (rr < H) {
-          if (found < kSphList) {
-            r[found] = rr;
-            jl[found] = j;
-          }
-          ++found;
-        }
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
+      const int take = __popc(__ballot_sync(0xffffffffu, lane < m && incl <= 32));
+      const int total = __shfl_sync(0xffffffffu, incl, take - 1);
+      sp -= take;
+      visits += total;
+      if (visits > A.max_visits) return ST_WALKCAP;
+      // lane s takes node s of the gathered ranges: r = ranges ending at or before s
+      int r = 0;
+#pragma unroll
+      for (int b = 16; b > 0; b >>= 1) {
+        const int cand = r + b;
+        const int v = __shfl_sync(0xffffffffu, incl, (cand - 1) & 31);
+        if (cand <= take && v <= lane) r = cand;
+      }
+      const int prev = __shfl_sync(0xffffffffu, incl, (r - 1) & 31);
+      const int excl = r > 0 ? prev : 0;
+      const int rfirst = __shfl_sync(0xffffffffu, rfirst_l, r & 31);
+      const bool has = lane < total;
+      const int node = has ? rfirst + (lane - excl) : 0;
+      if (__any_sync(0xffffffffu, has && (node < 0 || node >= nodes_total))) return ST_TREELINK;
+      const float4 NC = T.nC[node];
+      const int4 ND = T.nD[node];
+      bool keep = false;
+      if (has) {
+        const float hs = 0.5f * NC.w;
+        const float gx = fmaxf(fabsf(sph_mi1(NC.x - G.cx)) - (hs + G.ex), 0.f);
+        const float gy = fmaxf(fabsf(sph_mi1(NC.y - G.cy)) - (hs + G.ey), 0.f);
+        const float gz = fmaxf(fabsf(sph_mi1(NC.z - G.cz)) - (hs + G.ez), 0.f);
+        keep = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= R2;
+      }
+      const bool leaf = meta_leaf(ND.w);
+      const int nch = meta_nchild(ND.w);
+      bool bad = false;
+      if (keep) {
+        if (leaf) bad = ND.x < 0 || ND.y < 1 || (int64_t)ND.x + ND.y > T.n;
+        else bad = nch <= 0 || nch > 8 || ND.z <= node || ND.z + nch > nodes_total;
+      }
+      if (__any_sync(0xffffffffu, bad)) return ST_TREELINK;
+      const bool push = keep && !leaf;
+      const uint32_t pm = __ballot_sync(0xffffffffu, push);
+      if (push) W.stack[sp + __popc(pm & lt)] = (int)((uint32_t)ND.z | ((uint32_t)nch << 28));
+      sp += __popc(pm);
+      const bool q = keep && leaf;
+      const uint32_t qm = __ballot_sync(0xffffffffu, q);
+      if (q) W.queue[nq + __popc(qm & lt)] = make_int2(ND.x, ND.y);
+      nq += __popc(qm);
+      __syncwarp();
+    } else if (nq > 0) {
+      // slot offsets of the queued leaves (warp scan, 32 entries at a time)
+      int run = 0;
+      for (int b0 = 0; b0 < nq; b0 += 32) {
+        const int e = b0 + lane;
+        const int c = e < nq ? W.queue[e].y : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (e < nq) W.qoff[e] = run + incl - c;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      __syncwarp();
+      // stage the candidates 32 at a time (one coalesced load per lane) and
+      // let every lane evaluate them from shared memory
+      for (int s0 = 0; s0 < run; s0 += 32) {
+        const int slot = s0 + lane;
+        if (slot < run) {
+          int lo = 0, hi = nq - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (W.qoff[mid] <= slot) lo = mid; else hi = mid - 1;
+          }
+          const int j = W.queue[lo].x + (slot - W.qoff[lo]);
+          W.sa[lane] = T.pA[j];
+          W.sb[lane] = T.pB[j];
+          W.sj[lane] = j;
+        }
+        __syncwarp();
+        eval(W, min(32, run - s0));
+        __syncwarp();
+      }
+      nq = 0;
     } else {
-      const int nc = meta_nchild(D.w);
-      if (sp + nc > kSphStack) return -1;
-      for (int c2 = 0; c2 < nc; ++c2) stack[sp++] = D.z + c2;
+      break;
     }
   }
-  return found;
+  return 0u;
 }
 
-__device__ __forceinline__ double sph_neff(const double* r, int cnt, double h) {
-  double s = 0.0;
-  for (int k = 0; k < cnt; ++k) s += sph_w(r[k] / h);
-  return (32.0 / 3.0) * s;
+// Split-float squared distance (box units) from a target to a staged particle.
+__device__ __forceinline__ float sph_r2_32(const float3& th, const float3& tl, const float4& a, const float4& b) {
+  const float dx = sph_mi1(th.x - a.x) + (tl.x - b.x);
+  const float dy = sph_mi1(th.y - a.y) + (tl.y - b.y);
+  const float dz = sph_mi1(th.z - a.z) + (tl.z - b.z);
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
-__global__ void __launch_bounds__(128) k_sph_density(SphArgs A) {
+// FP32 pass: sums of w(q) and q w'(q) over the particles within h.
+struct SphEval32 {
+  float3 th, tl;
+  float h2, ih2;  // h^2, 1 / h^2 (box units)
+  float S0, S1;
+  __device__ __forceinline__ void operator()(const SphBufs& W, int count) {
+    for (int s = 0; s < count; ++s) {
+      const float r2 = sph_r2_32(th, tl, W.sa[s], W.sb[s]);
+      if (r2 < h2) {
+        float w, wq;
+        spline_w32(sqrtf(r2 * ih2), w, wq);
+        S0 += w;
+        S1 += wq;
+      }
+    }
+  }
+};
+
+// FP64 pass: candidates within hb (FP32 test with a margin) go to this lane's
+// list; a full list anywhere in the warp is flushed, i.e. every lane
+// evaluates its listed candidates in FP64.
+struct SphEval64 {
+  const SphArgs* A;
+  const SphBufs* W;
+  int lane;
+  int64_t k;           // this lane's sorted index
+  float3 th, tl;
+  float hb2_32;        // FP32 prefilter radius^2 (box units), with margin
+  double x[3];         // target position (physical, wrapped)
+  double h, ih, hlo, hhi;  // evaluated h, 1 / h, band [hlo, hhi) (physical)
+  double S0, S1, R0, R1;
+  double br0, br1;     // the first two neighbour distances in the band
+  int clt, band, cnt;
+  __device__ __forceinline__ void flush() {
+    const TreeDev& T = A->T;
+    const double L = A->B.L, hL = 0.5 * L;
+    const int top = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
+    for (int t = 0; t < top; ++t) {
+      if (t < cnt) {
+        const int j = W->list[t][lane];
+        double d[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          double v = x[c] - T.x64[3 * (int64_t)j + c];
+          if (v > hL) v -= L;
+          else if (v < -hL) v += L;
+          d[c] = v;
+        }
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+        // r = r2 / sqrt(r2) with the reciprocal square root from its FP32
+        // approximation and one Newton-Raphson step, y <- y (3 - r2 y^2) / 2
+        double r = 0.0;
+        if (r2 > 0.0) {
+          const double y0 = (double)rsqrtf((float)r2);
+          const double y1 = y0 * fma(-0.5 * r2, y0 * y0, 1.5);
+          r = r2 * y1;
+        }
+        if (r < hhi) {
+          double w, wq;
+          spline_w64(r * ih, w, wq);
+          const double m = T.m64[j];
+          S0 += w;
+          S1 += wq;
+          R0 = fma(m, w, R0);
+          R1 = fma(m, wq, R1);
+          if (j != (int)k) {
+            if (r < h) ++clt;
+            if (r >= hlo) {
+              if (band == 0) br0 = r;
+              else if (band == 1) br1 = r;
+              ++band;
+            }
+          }
+        }
+      }
+    }
+    cnt = 0;
+    __syncwarp();
+  }
+  __device__ __forceinline__ void operator()(const SphBufs& Wb, int count) {
+    for (int s = 0; s < count; ++s) {
+      const float r2 = sph_r2_32(th, tl, Wb.sa[s], Wb.sb[s]);
+      if (r2 < hb2_32) W->list[cnt++][lane] = Wb.sj[s];
+      if (__any_sync(0xffffffffu, cnt == kSphList)) {
+        __syncwarp();
+        flush();
+      }
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
+  __shared__ int s_stack[kSphWarps][kSphStack];
+  __shared__ int2 s_queue[kSphWarps][kSphQueue];
+  __shared__ int s_list[kSphWarps][kSphList][32];
+  __shared__ int s_qoff[kSphWarps][kSphQueue + 1];
+  __shared__ float4 s_sa[kSphWarps][32];
+  __shared__ float4 s_sb[kSphWarps][32];
+  __shared__ int s_sj[kSphWarps][32];
   const TreeDev& T = A.T;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if (T.sb->status != 0 || T.sb->magic != kMagicTree) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(A.wsb, ST_NOTREE);
+    // a failed or missing tree: flag it and write NaN / -1 everywhere
+    if (threadIdx.x == 0) set_status(A.wsb, ST_NOTREE);
+    for (int64_t kk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; kk < T.n;
+         kk += (int64_t)gridDim.x * blockDim.x) {
+      A.h_out[kk] = NAN;
+      A.rho_out[kk] = NAN;
+      A.ngb_out[kk] = -1;
+    }
     return;
   }
-  double r[kSphList];
-  int jl[kSphList];
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < T.n; k += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t i = T.order[k];
-    double x[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] = div_box(T.x64[3 * k + a], A.B);
-    double H = A.h0 < 0.5 ? A.h0 : 0.5;
-    int cnt = -1;
-    bool ok = false;
-    for (int t = 0; t < kSphTries; ++t) {
-      cnt = sph_gather(A, x, H, r, jl);
-      if (cnt < 0) break;
-      if (cnt > kSphList) {  // too many within H: narrow it
-        H *= 0.7;
-        continue;
-      }
-      if (sph_neff(r, cnt, H) >= A.n_ngb) {
-        ok = true;
+  const int64_t g = (int64_t)blockIdx.x * kSphWarps + wib;
+  if (g >= T.ngroups) return;
+  SphBufs W;
+  W.stack = s_stack[wib];
+  W.queue = s_queue[wib];
+  W.list = s_list[wib];
+  W.qoff = s_qoff[wib];
+  W.sa = s_sa[wib];
+  W.sb = s_sb[wib];
+  W.sj = s_sj[wib];
+  int nodes_total = 0;
+  for (int l = 0; l < kLevels; ++l) nodes_total += T.sb->level_cnt[l];
+  if (nodes_total > T.cap) nodes_total = (int)T.cap;
+
+  const int64_t k = g * kGroup + lane;
+  const bool valid = k < T.n;
+  const int64_t kc = valid ? k : 0;
+  SphGroup G;
+  {
+    const float4 lo = T.gbox[2 * g], hi = T.gbox[2 * g + 1];
+    G.cx = 0.5f * (lo.x + hi.x);
+    G.cy = 0.5f * (lo.y + hi.y);
+    G.cz = 0.5f * (lo.z + hi.z);
+    G.ex = 0.5f * (hi.x - lo.x) * 1.0001f + 1e-7f;
+    G.ey = 0.5f * (hi.y - lo.y) * 1.0001f + 1e-7f;
+    G.ez = 0.5f * (hi.z - lo.z) * 1.0001f + 1e-7f;
+  }
+  const float4 pa = T.pA[kc], pb = T.pB[kc];
+  const float3 th = make_float3(pa.x, pa.y, pa.z), tl = make_float3(pb.x, pb.y, pb.z);
+  const float nngb = (float)A.n_ngb;
+
+  // 1. start: the density of the smallest ancestor holding >= N_ngb particles
+  float h = 0.5f;
+  {
+    int p = T.leaf_of[kc];
+    for (int up = 0; up < kLevels + 1 && p >= 0 && p < nodes_total; ++up) {
+      const int c = T.nD[p].y;
+      if ((double)c >= A.n_ngb || T.nParent[p] < 0) {
+        const float s = T.nC[p].w;
+        h = s * cbrtf(3.0f * nngb / (4.0f * 3.14159265f * (float)c));
         break;
       }
-      if (H >= 0.5) break;  // the minimum image allows no wider sphere
-      H = H * 1.6 < 0.5 ? H * 1.6 : 0.5;
+      p = T.nParent[p];
     }
-    if (!ok) {
-      set_status(A.wsb, cnt < 0 ? ST_TREELINK : ST_WALKCAP);
-      A.h_out[i] = NAN;
-      A.rho_out[i] = NAN;
-      A.ngb_out[i] = -1;
-      continue;
+    h = fminf(fmaxf(h, 1e-7f), 0.5f);
+  }
+
+  // 2. FP32 Newton passes on ln h
+  bool conv = !valid, fail = false;
+  float blo = 0.f, bhi = 1e30f;
+  uint32_t st = 0;
+  for (int pass = 0; pass < kSphPass32 && __any_sync(0xffffffffu, !conv); ++pass) {
+    const float Rl = conv ? 0.f : h;
+    const float R = __int_as_float((int)__reduce_max_sync(0xffffffffu, (unsigned)__float_as_int(Rl)));
+    SphEval32 ev;
+    ev.th = th;
+    ev.tl = tl;
+    ev.h2 = h * h;
+    ev.ih2 = 1.0f / (h * h);
+    ev.S0 = 0.f;
+    ev.S1 = 0.f;
+    st |= sph_gather(A, W, G, R, nodes_total, lane, ev);
+    if (st) break;
+    if (!conv) {
+      const float N = (32.0f / 3.0f) * ev.S0;
+      if (N < nngb) blo = h;
+      else bhi = h;
+      float dl;
+      if (ev.S1 < 0.f) dl = (__logf(N) - __logf(nngb)) * ev.S0 / ev.S1;
+      else dl = N >= nngb ? -0.7f : 0.7f;
+      dl = fminf(fmaxf(dl, -0.7f), 0.7f);
+      if (h >= 0.5f && N < nngb) {
+        fail = true;  // no root below half the box
+        conv = true;
+      } else if (fabsf(dl) < 1e-5f) {
+        // converged: take the Newton step itself (it may round to h, which
+        // is a bracket end by now, so it is not tested against the bracket)
+        h = fminf(h * __expf(dl), 0.5f);
+        conv = true;
+      } else {
+        float hn = h * __expf(dl);
+        if (blo > 0.f && bhi < 1e30f && !(hn > blo && hn < bhi)) hn = sqrtf(blo * bhi);
+        if (hn > 0.5f) hn = 0.5f;
+        conv = bhi < 1e30f && bhi - blo < 2e-6f * bhi;
+        h = hn;
+      }
     }
-    // N_eff is increasing in h: bisect [0, H] to the FP64 resolution of H
-    double lo = 0.0, hi = H;
-    for (int s = 0; s < kSphBisect && hi - lo > 1e-12 * hi; ++s) {
-      const double mid = 0.5 * (lo + hi);
-      if (sph_neff(r, cnt, mid) < A.n_ngb) lo = mid;
-      else hi = mid;
+  }
+
+  // 3. FP64 pass(es): Newton step, density and neighbour count
+  const double L = A.B.L;
+  bool done = !valid || fail;
+  double hd = (double)h * L;
+  double lo64 = 0.0, hi64 = 0.0;  // FP64 bracket (hi64 = 0: none yet)
+  double h_out = NAN, rho_out = NAN;
+  int ngb_out = -1;
+  double xk[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) xk[c] = T.x64[3 * kc + c];
+  for (int pass = 0; pass < kSphPass64 && !st && __any_sync(0xffffffffu, !done); ++pass) {
+    SphEval64 ev;
+    ev.A = &A;
+    ev.W = &W;
+    ev.lane = lane;
+    ev.k = k;
+    ev.th = th;
+    ev.tl = tl;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ev.x[c] = xk[c];
+    ev.h = hd;
+    ev.ih = 1.0 / hd;
+    ev.hlo = hd * (1.0 - 4e-6);
+    ev.hhi = hd * (1.0 + 4e-6);
+    const float hb = (float)(ev.hhi / L);
+    ev.hb2_32 = done ? -1.f : hb * hb * 1.0001f + 1e-14f;
+    ev.S0 = ev.S1 = ev.R0 = ev.R1 = 0.0;
+    ev.clt = ev.band = ev.cnt = 0;
+    ev.br0 = ev.br1 = 0.0;
+    const float Rl = done ? 0.f : hb;
+    const float R = __int_as_float((int)__reduce_max_sync(0xffffffffu, (unsigned)__float_as_int(Rl)));
+    st |= sph_gather(A, W, G, R, nodes_total, lane, ev);
+    if (st) break;
+    ev.flush();
+    if (!done) {
+      const double N = (32.0 / 3.0) * ev.S0;
+      if (N < A.n_ngb) lo64 = hd;
+      else hi64 = hd;
+      double hn;
+      if (ev.S1 < 0.0) hn = hd + (N - A.n_ngb) * hd / ((32.0 / 3.0) * ev.S1);
+      else hn = N >= A.n_ngb ? 0.5 * hd : 2.0 * hd;
+      const bool small = fabs(hn - hd) <= 3e-6 * hd;
+      if (!small && hi64 > 0.0 && lo64 > 0.0 && !(hn > lo64 && hn < hi64)) hn = 0.5 * (lo64 + hi64);
+      if (small && (ev.band <= 2 || hn == hd)) {
+        // the step stays inside the band, so only band neighbours can change
+        // side between hd and hn
+        int c = ev.clt;
+        if (ev.band >= 1) c += (int)(ev.br0 < hn) - (int)(ev.br0 < hd);
+        if (ev.band >= 2) c += (int)(ev.br1 < hn) - (int)(ev.br1 < hd);
+        const double R0f = ev.R0 - ev.R1 * (hn - hd) / hd;
+        h_out = hn;
+        rho_out = 8.0 * R0f / (M_PI * hn * hn * hn);
+        ngb_out = c;
+        done = true;
+      } else {
+        hd = hn > 0.5 * L ? 0.5 * L : hn;
+      }
     }
-    const double h = hi;
-    double rho = 0.0;
-    int ngb = 0;
-    for (int q = 0; q < cnt; ++q) {
-      rho += T.m64[jl[q]] * sph_w(r[q] / h);
-      if (r[q] < h && jl[q] != (int)k) ++ngb;
+  }
+  if (st && lane == 0) set_status(A.wsb, st);
+  if (valid) {
+    if (!done || fail || st) {
+      if (!st) set_status(A.wsb, ST_WALKCAP);
+      h_out = NAN;
+      rho_out = NAN;
+      ngb_out = -1;
     }
-    const double hL = h * A.B.L;
-    A.h_out[i] = hL;
-    A.rho_out[i] = rho * 8.0 / (M_PI * hL * hL * hL);
-    A.ngb_out[i] = ngb;
+    const int32_t i = T.order[k];
+    A.h_out[i] = h_out;
+    A.rho_out[i] = rho_out;
+    A.ngb_out[i] = ngb_out;
   }
 }
 
@@ -176,21 +528,21 @@ og_status og_sph_density(const og_tree* t, double n_ngb, void* ws, size_t ws_byt
   if (!std::isfinite(n_ngb) || n_ngb <= 0.0) return OG_EINVAL;
   if ((reinterpret_cast<uintptr_t>(ws) % og::kAlign) != 0) return OG_EINVAL;
   if (ws_bytes < og_sph_ws_bytes()) return OG_ENOSPACE;
+  if (t->node_capacity >= (int64_t(1) << 28)) return OG_EINVAL;  // node indices are packed in 28 bits
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   og::SphArgs A;
   A.T = og::tree_view(t);
   A.wsb = static_cast<og::StatusBlock*>(ws);
   A.B = og::box_scale(t->box);
   A.n_ngb = n_ngb;
-  // the radius that holds n_ngb neighbours at the mean density, in box units
-  A.h0 = std::cbrt(3.0 * n_ngb / (4.0 * M_PI * (double)t->n));
+  A.max_visits = t->max_walk_iters;
   A.h_out = h;
   A.rho_out = rho;
   A.ngb_out = ngb;
   if (cudaMemsetAsync(A.wsb, 0, sizeof(og::StatusBlock), s) != cudaSuccess) return OG_ECUDA;
-  int64_t grid = (t->n + 127) / 128;
-  if (grid > og::grid_cap(16)) grid = og::grid_cap(16);
-  og::k_sph_density<<<(unsigned)grid, 128, 0, s>>>(A);
+  const int64_t grid = (t->n_groups + og::kSphWarps - 1) / og::kSphWarps;
+  if (grid <= 0) return OG_OK;
+  og::k_sph_density<<<(unsigned)grid, og::kSphWarps * 32, 0, s>>>(A);
   return cudaGetLastError() == cudaSuccess ? OG_OK : OG_ECUDA;
 }
 

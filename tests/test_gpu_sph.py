@@ -1,9 +1,11 @@
 """SPH density on the device against the FP64 oracle (oracle/og_sph.py).
 
-Both sides solve N_eff(h) = N_ngb by bisection to 1e-12 of the bracket in
-FP64, on the same minimum-image distances (the device's in box units).  So
-h and rho agree to 1e-9 relative, and neighbour counts exactly (ties at
-r = h have measure zero).
+The oracle solves N_eff(h) = N_ngb by FP64 bisection to 1e-12 of h.  The
+device's grouped walk converges in FP32 (to ~1e-6) and finishes with one
+FP64 Newton step on FP64 minimum-image distances (error ~1e-11), with the
+density carried to the new h to first order (~1e-11).  So h and rho agree
+to 1e-9 relative, and neighbour counts exactly (ties at r = h have measure
+zero).
 """
 import numpy as np
 import pytest
@@ -80,3 +82,20 @@ def test_too_many_neighbours_is_flagged():
     tree = m.tree_build(keys, order, pos, mass, 1e-3, 1.0)
     with pytest.raises(m.OGError):
         m.sph_density(tree, 500.0)  # more than a half-box sphere can hold
+
+
+def test_clustered_set_full_tree_depth():
+    """A clustered set large enough for haloes much denser than the mean
+    (the start radius comes from the tree, and Newton steps span decades)."""
+    dev = device()
+    w = ics.make("nfw256", 48)   # 110,592 particles
+    _compare(w.pos, w.mass, w.box, 32, dev, nsamp=60, seed=5)
+
+
+def test_small_and_ragged():
+    """Fewer particles than a group, and a ragged last group."""
+    dev = device()
+    rng = np.random.default_rng(6)
+    for n in (40, 1000 + 17):
+        pos = rng.random((n, 3))
+        _compare(pos, np.full(n, 1.0 / n), 1.0, 16, dev, nsamp=40, seed=n)
