@@ -138,7 +138,10 @@ og_status og_keys_sort(const double* pos, int64_t n, double box, uint64_t* keys_
 /*
  * og_tree_build -- octree with monopole moments over the sorted particles.
  *
- * A node is a maximal run of sorted keys that share their top 3*level bits
+ * The paper's gravity solver walks a Barnes-Hut tree that the host builds
+ * and offloads to the GPU every step (Sec. 2.1, and the offloaded tree
+ * structures of Appendix A); here the tree is built on the device from the
+ * sorted keys.  A node is a maximal run of sorted keys that share their top 3*level bits
  * (the cell at that level); a node with more than leaf_size particles below
  * level 21 is split into its non-empty octants.  Per node: member range,
  * mass M = sum m (FP64), centre of mass sum(m x)/M (FP64), geometric centre
@@ -187,6 +190,9 @@ og_status og_shortrange_accel(const og_tree* t, double r_s, double theta, og_pre
 /*
  * og_shortrange_adjoint -- dL/dx and dL/dm for L = sum_i w_i . a_i.
  *
+ * The paper has no adjoint: this call differentiates the walk of
+ * og_shortrange_accel (Sec. 2, 3.1: the Barnes-Hut short-range force) with
+ * respect to positions and masses, for a loss linear in the accelerations.
  * The opening, cut and softening decisions of og_shortrange_accel are frozen
  * (recomputed deterministically by the same walk).  With g(d) = -F(r) d and
  * J = dg/dd = -F I - (F'/r) d d^T:
