@@ -214,6 +214,36 @@ og_status og_shortrange_adjoint(const og_tree* t, double r_s, double theta, og_p
                                 og_stream stream);
 
 /*
+ * og_shortrange_accel_range / og_shortrange_adjoint_range -- the same walks
+ * over the walk groups [g_begin, g_end) only, i.e. over the targets with
+ * sorted indices [32 g_begin, min(32 g_end, n)): a contiguous range of
+ * Peano-Hilbert keys.
+ *
+ * The paper distributes the walk over MPI ranks by domain, exchanging the
+ * particles a rank's targets need (Sec. 2).  These calls are the per-rank
+ * part of a key-range decomposition in which every rank holds the same tree
+ * (built from all positions) and walks its own range of groups; the
+ * package's KeyRangeDecomposition does the collectives.
+ *
+ * accel_range: like og_shortrange_accel, but only the range's targets are
+ *   written (acc, counts: original order; entries of other particles are
+ *   left untouched); n_interact counts the range's interactions.
+ * adjoint_range: the gradient of the partial loss L_r = sum over the range's
+ *   targets i of w_i . a_i (w of other targets is ignored), for every
+ *   particle: dpos and dmass are fully written.  The gradients of the ranges
+ *   of a partition of [0, n_groups) add up to og_shortrange_adjoint's.
+ * 0 <= g_begin <= g_end <= n_groups, else OG_EINVAL; an empty range writes
+ *   nothing (accel) or zero gradients (adjoint).  Everything else as for the
+ *   full calls.
+ */
+og_status og_shortrange_accel_range(const og_tree* t, double r_s, double theta, og_precision prec,
+                                    int64_t g_begin, int64_t g_end, void* acc, uint64_t* n_interact,
+                                    int32_t* counts, void* ws, size_t ws_bytes, og_stream stream);
+og_status og_shortrange_adjoint_range(const og_tree* t, double r_s, double theta, og_precision prec, const float* w,
+                                      int64_t g_begin, int64_t g_end, double* dpos, double* dmass,
+                                      int recompute_lists, void* ws, size_t ws_bytes, og_stream stream);
+
+/*
  * og_keys_sort_noalloc -- og_keys_sort for callers that cannot allocate.
  *
  * The paper has no counterpart: this is a convenience of this library.  Some

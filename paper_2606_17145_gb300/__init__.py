@@ -178,8 +178,10 @@ def tree_build(keys: torch.Tensor, order: torch.Tensor, pos: torch.Tensor, mass:
 
 def shortrange_accel(tree: Tree, r_s: float, theta: float, prec: str = "fp32", counts: bool = False,
                      stream=None, check: bool = True, ws: torch.Tensor | None = None, out: torch.Tensor | None = None,
-                     total: torch.Tensor | None = None):
-    """Short-range accelerations (original order).  Returns (acc, total, counts)."""
+                     total: torch.Tensor | None = None, groups: tuple[int, int] | None = None):
+    """Short-range accelerations (original order).  Returns (acc, total, counts).
+    groups=(g0, g1): walk only the groups [g0, g1) (og_shortrange_accel_range);
+    only those targets' rows of acc / counts are written."""
     L = lib()
     code = N.OG_FP64 if prec == "fp64" else N.OG_FP32_KAHAN
     dev = tree.mem.device
@@ -191,8 +193,13 @@ def shortrange_accel(tree: Tree, r_s: float, theta: float, prec: str = "fp32", c
     cnt = torch.empty(n, dtype=torch.int32, device=dev) if counts else None
     if ws is None:
         ws = _workspace(L.og_accel_ws_bytes(C.byref(tree.header), code), dev)
-    _check(L.og_shortrange_accel(C.byref(tree.header), float(r_s), float(theta), code, _ptr(out), _ptr(total),
-                                 _ptr(cnt), _ptr(ws), ws.numel(), _stream(stream)), "og_shortrange_accel")
+    if groups is None:
+        _check(L.og_shortrange_accel(C.byref(tree.header), float(r_s), float(theta), code, _ptr(out), _ptr(total),
+                                     _ptr(cnt), _ptr(ws), ws.numel(), _stream(stream)), "og_shortrange_accel")
+    else:
+        _check(L.og_shortrange_accel_range(C.byref(tree.header), float(r_s), float(theta), code, int(groups[0]),
+                                           int(groups[1]), _ptr(out), _ptr(total), _ptr(cnt), _ptr(ws), ws.numel(),
+                                           _stream(stream)), "og_shortrange_accel_range")
     if check:
         _check(poll_status(ws, stream), "og_shortrange_accel (device)")
     return out, total, cnt
@@ -200,8 +207,10 @@ def shortrange_accel(tree: Tree, r_s: float, theta: float, prec: str = "fp32", c
 
 def shortrange_adjoint(tree: Tree, r_s: float, theta: float, w: torch.Tensor, stream=None, check: bool = True,
                        ws: torch.Tensor | None = None, dpos: torch.Tensor | None = None,
-                       dmass: torch.Tensor | None = None):
-    """dL/dx [n,3] and dL/dm [n] (float64, original order) for L = sum w . a."""
+                       dmass: torch.Tensor | None = None, groups: tuple[int, int] | None = None):
+    """dL/dx [n,3] and dL/dm [n] (float64, original order) for L = sum w . a.
+    groups=(g0, g1): the gradient of the partial loss over the targets of the
+    groups [g0, g1) only (og_shortrange_adjoint_range)."""
     _cuda(w, torch.float32, (3,), "w")
     L = lib()
     dev = tree.mem.device
@@ -212,9 +221,14 @@ def shortrange_adjoint(tree: Tree, r_s: float, theta: float, w: torch.Tensor, st
         dpos = torch.empty((n, 3), dtype=torch.float64, device=dev)
     if dmass is None:
         dmass = torch.empty(n, dtype=torch.float64, device=dev)
-    _check(L.og_shortrange_adjoint(C.byref(tree.header), float(r_s), float(theta), N.OG_FP32_KAHAN, _ptr(w),
-                                   _ptr(dpos), _ptr(dmass), 1, _ptr(ws), ws.numel(), _stream(stream)),
-           "og_shortrange_adjoint")
+    if groups is None:
+        _check(L.og_shortrange_adjoint(C.byref(tree.header), float(r_s), float(theta), N.OG_FP32_KAHAN, _ptr(w),
+                                       _ptr(dpos), _ptr(dmass), 1, _ptr(ws), ws.numel(), _stream(stream)),
+               "og_shortrange_adjoint")
+    else:
+        _check(L.og_shortrange_adjoint_range(C.byref(tree.header), float(r_s), float(theta), N.OG_FP32_KAHAN,
+                                             _ptr(w), int(groups[0]), int(groups[1]), _ptr(dpos), _ptr(dmass), 1,
+                                             _ptr(ws), ws.numel(), _stream(stream)), "og_shortrange_adjoint_range")
     if check:
         _check(poll_status(ws, stream), "og_shortrange_adjoint (device)")
     return dpos, dmass

@@ -165,11 +165,22 @@ static og_status walk_common(const og_tree* t, double r_s, double theta, WalkArg
 
 og_status og_shortrange_accel(const og_tree* t, double r_s, double theta, og_precision prec, void* acc,
                               uint64_t* n_interact, int32_t* counts, void* ws, size_t ws_bytes, og_stream stream) {
+  if (!t) return OG_ETREE;
+  return og_shortrange_accel_range(t, r_s, theta, prec, 0, t->n_groups, acc, n_interact, counts, ws, ws_bytes,
+                                   stream);
+}
+
+og_status og_shortrange_accel_range(const og_tree* t, double r_s, double theta, og_precision prec,
+                                    int64_t g_begin, int64_t g_end, void* acc, uint64_t* n_interact,
+                                    int32_t* counts, void* ws, size_t ws_bytes, og_stream stream) {
   if (!acc || !ws) return OG_EINVAL;
   if (prec != OG_FP32_KAHAN && prec != OG_FP64) return OG_EINVAL;
   WalkArgs A;
   og_status st = walk_common(t, r_s, theta, A);
   if (st != OG_OK) return st;
+  if (g_begin < 0 || g_end < g_begin || g_end > t->n_groups) return OG_EINVAL;
+  A.g_begin = g_begin;
+  A.g_end = g_end;
   if (!aligned(ws)) return OG_EINVAL;
   if (ws_bytes < og_accel_ws_bytes(t, prec)) return OG_ENOSPACE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -187,12 +198,23 @@ og_status og_shortrange_accel(const og_tree* t, double r_s, double theta, og_pre
 og_status og_shortrange_adjoint(const og_tree* t, double r_s, double theta, og_precision prec, const float* w,
                                 double* dpos, double* dmass, int recompute_lists, void* ws, size_t ws_bytes,
                                 og_stream stream) {
+  if (!t) return OG_ETREE;
+  return og_shortrange_adjoint_range(t, r_s, theta, prec, w, 0, t->n_groups, dpos, dmass, recompute_lists, ws,
+                                     ws_bytes, stream);
+}
+
+og_status og_shortrange_adjoint_range(const og_tree* t, double r_s, double theta, og_precision prec, const float* w,
+                                      int64_t g_begin, int64_t g_end, double* dpos, double* dmass,
+                                      int recompute_lists, void* ws, size_t ws_bytes, og_stream stream) {
   if (!w || !dpos || !dmass || !ws) return OG_EINVAL;
   if (prec != OG_FP32_KAHAN) return prec == OG_FP64 ? OG_ENOTIMPL : OG_EINVAL;
   if (recompute_lists != 1) return recompute_lists == 0 ? OG_ENOTIMPL : OG_EINVAL;
   WalkArgs A;
   og_status st = walk_common(t, r_s, theta, A);
   if (st != OG_OK) return st;
+  if (g_begin < 0 || g_end < g_begin || g_end > t->n_groups) return OG_EINVAL;
+  A.g_begin = g_begin;
+  A.g_end = g_end;
   if (!aligned(ws)) return OG_EINVAL;
   const size_t need = og_adjoint_ws_bytes(t, recompute_lists);
   if (ws_bytes < need) return OG_ENOSPACE;

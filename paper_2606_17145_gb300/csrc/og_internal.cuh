@@ -299,6 +299,7 @@ struct WalkArgs {
   StatusBlock* wsb;
   long long max_iters;
   int deep;                    // stack depth above which a step pops one range (<= the compiled bound)
+  int64_t g_begin, g_end;      // walk groups [g_begin, g_end) (a key range of targets)
   // FP32, box units
   float rc2, rc2_lo, rc2_hi;   // node tests: rcut^2 and its relative band
   float pp_lo, pp_hi;          // pair cut band

@@ -933,24 +933,30 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   __shared__ float4 s_sgb[kWarpsPerBlock][2 * kSub];
   const TreeDev& T = A.T;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t g = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
-  if (g >= T.ngroups) return;
+  const int64_t g = A.g_begin + (int64_t)blockIdx.x * kWarpsPerBlock + wib;
+  if (g >= A.g_end) return;
   if (T.sb->status != 0 || T.sb->magic != kMagicTree) {
-    // a failed or missing tree: flag it and give every output NaN (each
-    // index k < n is written by exactly one lane; no permutation is read),
-    // so that nothing downstream can take stale values for forces
+    // a failed or missing tree: flag it and give every output of this
+    // group's targets NaN, so that nothing downstream can take stale values
+    // for forces.  A tree whose build started wrote its permutation first;
+    // for one that was never built the sorted index stands in for it.
     if (lane == 0) set_status(A.wsb, ST_NOTREE);
     const int64_t kk = g * kGroup + lane;
     if (kk < T.n) {
       const float nf = __int_as_float(0x7fc00000);
       const double nd = __longlong_as_double(0x7ff8000000000000ll);
+      int64_t io = kk;
+      if (T.sb->magic == kMagicTree) {
+        const int64_t o = T.order[kk];
+        if (o >= 0 && o < T.n) io = o;
+      }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        if (A.accf) A.accf[3 * kk + c] = nf;
-        if (A.accd) A.accd[3 * kk + c] = nd;
+        if (A.accf) A.accf[3 * io + c] = nf;
+        if (A.accd) A.accd[3 * io + c] = nd;
         if (A.tgt) A.tgt[3 * kk + c] = nd;
       }
-      if (A.counts) A.counts[kk] = -1;
+      if (A.counts) A.counts[io] = -1;
     }
     return;
   }
@@ -1204,7 +1210,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
 }
 
 cudaError_t launch_walk(const WalkArgs& A, int prec, bool adjoint, cudaStream_t s) {
-  const int64_t blocks = (A.T.ngroups + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int64_t blocks = (A.g_end - A.g_begin + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks <= 0) return cudaSuccess;
   if (adjoint) k_walk<LaneF32<true>><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(A);
   else if (prec == OG_FP64) k_walk<LaneF64><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(A);
