@@ -381,6 +381,8 @@ def main():
     ap.add_argument("--side", default="zeldovich128,zoom8m",
                     help="other workloads timed beside the line (comma list, empty for none)")
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel instead of replaying a CUDA graph")
+    ap.add_argument("--scale", type=int, default=None,
+                    help="a smaller instance of the workload (particles per side; for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -390,7 +392,7 @@ def main():
 
     import numpy as np
     import ics
-    w = ics.make(args.workload)
+    w = ics.make(args.workload, args.scale)
 
     if args.impl == "reference":
         return run_reference(args, w, ws, rank)
@@ -643,7 +645,7 @@ def main():
                           "frac_fp64_measured": r64 * FP64_FLOPS / 1e12 / peaks["fp64_tflops"]}
     dom = max(("accel_fp32", "adjoint_fp32"), key=lambda k: kern[k]["ms"])
     dk = kern[dom]
-    traffic = walk_traffic("forward" if dom == "accel_fp32" else "adjoint", args.workload)
+    traffic = None if args.scale else walk_traffic("forward" if dom == "accel_fp32" else "adjoint", args.workload)
     roofline = {"bound": "alu", "achieved": dk["tflops_algorithmic"], "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": dk["tflops_algorithmic"] / alu_peak, "traffic": traffic, "kernel": dom,
                 "flops_per_interaction": ADJ_FLOPS if dom == "adjoint_fp32" else FWD_FLOPS,
@@ -702,14 +704,16 @@ def main():
     sph_ms = max_over_ranks(sph_local, ws, dev)
     if sph is None:
         sph = ({"ms": sph_ms, "particles_per_s": ws * n / (sph_ms * 1e-3), "n_ngb": n_ngb,
-                "what": "og_sph_density: tree gather, smoothing length by bisection, density"}
+                "what": "og_sph_density: grouped tree gather, smoothing length by FP32 Newton steps and one FP64 step, density"}
                if sph_ms < float("inf") else {"error": "failed on another rank"})
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "n": n, "theta": args.theta,
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}"
+                               + (f" (scaled down: {args.scale} per side)" if args.scale else ""),
+                   "n": n, "theta": args.theta,
                    "step": "keys_sort + tree_build + accel_fp32 + adjoint_fp32 (inputs resident)",
                    "l2": "inputs larger than L2; also flushed by a 256 MiB write between timed steps",
                    "parallelism": f"replicas x{ws}",
@@ -756,7 +760,9 @@ def main():
         oracle.build()
         t0 = time.time()
         T = oracle.Tree(w.pos, w.mass, 2.8 * w.eps)
+        build_s = time.time() - t0
         v, pps, sample, tg, a_or = oracle_throughput(w, args.theta, T=T)
+        sample = sample.replace("built once, 0.0 s", f"built once, {build_s:.1f} s")
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                                 "particles_per_s": pps, **host_info()}
         # error against the FP64 oracle: the tree at the same theta on the

@@ -24,12 +24,14 @@
 //      Distances come from the split-float positions (FP64 accuracy rounded
 //      to FP32).
 //   3. FP64 pass: each lane lists its candidates within h (1 + 4e-6) (FP32
-//      test with a margin) in shared memory, and the lists are evaluated
-//      lane-parallel in FP64 (the FP64 pipe is too narrow for lane-masked
-//      evaluation of every group candidate).  One Newton step from the FP32
-//      root gives h; the density at that h follows to first order from the
-//      sums at the evaluated h (the step is below 3e-6 h, so the neglected
-//      term is ~1e-11 relative); the neighbour count at the new h is the
+//      test with a margin) and their periodic image in shared memory, and the
+//      lists are evaluated lane-parallel in FP64 (the FP64 pipe is too narrow
+//      for lane-masked evaluation of every group candidate).  Only sum w and
+//      sum m w are taken in FP64.  One Newton step from the FP32 root gives
+//      h, with the derivative of the last FP32 pass (it scales a step below
+//      3e-6 h); the density at that h follows to first order from the sums
+//      at the evaluated h (neglected term ~1e-11 relative, the first-order
+//      term's derivative again from FP32); the neighbour count at the new h is the
 //      count at the evaluated one corrected by the neighbours within 4e-6 h
 //      of it (their distances are kept, up to two; with more the pass is
 //      repeated at the new h).
@@ -50,8 +52,8 @@ static_assert(kSphDeep + 31 + 7 * 20 + 8 <= kSphStack - kSphStackNeed, "stack bo
 constexpr int kSphQueue = 128;        // queued leaves per warp
 constexpr int kSphQueueNeed = 32;     // a step queues at most one leaf per popped node
 constexpr int kSphList = 32;          // FP64 pass: listed candidates per lane before a flush
-constexpr int kSphPass32 = 24;        // FP32 Newton passes at most
-constexpr int kSphPass64 = 4;         // FP64 passes at most
+constexpr int kSphPass32 = 32;        // FP32 Newton passes at most
+constexpr int kSphPass64 = 8;         // FP64 passes at most
 
 struct SphArgs {
   TreeDev T;
@@ -109,6 +111,7 @@ struct SphBufs {
   float4* sb;       // [32] lo part
   int* sj;          // [32] sorted index
   int (*list)[32];  // [kSphList][lane]
+  unsigned char (*img)[32];  // [kSphList][lane] periodic image code of each listed candidate
 };
 
 struct SphGroup {
@@ -240,27 +243,31 @@ __device__ __forceinline__ float sph_r2_32(const float3& th, const float3& tl, c
   return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
-// FP32 pass: sums of w(q) and q w'(q) over the particles within h.
+// FP32 pass: sums of w(q), q w'(q) and m q w'(q) over the particles within h.
 struct SphEval32 {
   float3 th, tl;
   float h2, ih2;  // h^2, 1 / h^2 (box units)
-  float S0, S1;
+  float S0, S1, R1;  // R1 in units of m / L^2 (the staged mass)
   __device__ __forceinline__ void operator()(const SphBufs& W, int count) {
     for (int s = 0; s < count; ++s) {
-      const float r2 = sph_r2_32(th, tl, W.sa[s], W.sb[s]);
+      const float4 a = W.sa[s];
+      const float r2 = sph_r2_32(th, tl, a, W.sb[s]);
       if (r2 < h2) {
         float w, wq;
         spline_w32(sqrtf(r2 * ih2), w, wq);
         S0 += w;
         S1 += wq;
+        R1 = fmaf(a.w, wq, R1);
       }
     }
   }
 };
 
 // FP64 pass: candidates within hb (FP32 test with a margin) go to this lane's
-// list; a full list anywhere in the warp is flushed, i.e. every lane
-// evaluates its listed candidates in FP64.
+// list with their periodic image; a full list anywhere in the warp is
+// flushed, i.e. every lane evaluates its listed candidates in FP64.  Only the
+// sums that set h and rho to 1e-12 are taken in FP64 (sum w, sum m w); the
+// derivatives, which scale a step below 3e-6 h, come from the FP32 pass.
 struct SphEval64 {
   const SphArgs* A;
   const SphBufs* W;
@@ -269,47 +276,50 @@ struct SphEval64 {
   float3 th, tl;
   float hb2_32;        // FP32 prefilter radius^2 (box units), with margin
   double x[3];         // target position (physical, wrapped)
-  double h, ih, hlo, hhi;  // evaluated h, 1 / h, band [hlo, hhi) (physical)
-  double S0, S1, R0, R1;
-  double br0, br1;     // the first two neighbour distances in the band
+  double ih2;          // 1 / h^2 (physical)
+  double S0, R0;
+  double bq0, bq1;     // q = r / h of the first two neighbours in the band
   int clt, band, cnt;
   __device__ __forceinline__ void flush() {
     const TreeDev& T = A->T;
-    const double L = A->B.L, hL = 0.5 * L;
+    const double L = A->B.L;
+    const double qhi2 = (1.0 + 4e-6) * (1.0 + 4e-6), qlo = 1.0 - 4e-6;
     const int top = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
     for (int t = 0; t < top; ++t) {
       if (t < cnt) {
         const int j = W->list[t][lane];
-        double d[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          double v = x[c] - T.x64[3 * (int64_t)j + c];
-          if (v > hL) v -= L;
-          else if (v < -hL) v += L;
-          d[c] = v;
-        }
-        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
-        // r = r2 / sqrt(r2) with the reciprocal square root from its FP32
-        // approximation and one Newton-Raphson step, y <- y (3 - r2 y^2) / 2
-        double r = 0.0;
-        if (r2 > 0.0) {
-          const double y0 = (double)rsqrtf((float)r2);
-          const double y1 = y0 * fma(-0.5 * r2, y0 * y0, 1.5);
-          r = r2 * y1;
-        }
-        if (r < hhi) {
-          double w, wq;
-          spline_w64(r * ih, w, wq);
-          const double m = T.m64[j];
+        const int code = W->img[t][lane];
+        // d = x_i - x_j - s L, s the image shift found in FP32 (one rounding,
+        // as the minimum-image definition d - L round(d / L))
+        const double s0 = (double)(code % 3 - 1), s1 = (double)((code / 3) % 3 - 1), s2 = (double)(code / 9 - 1);
+        const double d0 = fma(-s0, L, x[0] - T.x64[3 * (int64_t)j]);
+        const double d1 = fma(-s1, L, x[1] - T.x64[3 * (int64_t)j + 1]);
+        const double d2 = fma(-s2, L, x[2] - T.x64[3 * (int64_t)j + 2]);
+        const double q2 = fma(d0, d0, fma(d1, d1, d2 * d2)) * ih2;
+        if (q2 < qhi2) {
+          // q = sqrt(q2): FP32 seed and one Newton step, q0 + (q2 - q0^2) / (2 q0)
+          const float q0f = sqrtf((float)q2);
+          double q = 0.0;
+          if (q0f > 0.f) {
+            const double q0 = (double)q0f;
+            q = fma(fma(-q0, q0, q2), (double)__fdividef(0.5f, q0f), q0);
+          }
+          double w;
+          if (q <= 0.5) {
+            w = fma(q2, fma(6.0, q, -6.0), 1.0);
+          } else if (q < 1.0) {
+            const double u = 1.0 - q;
+            w = (2.0 * u) * (u * u);
+          } else {
+            w = 0.0;
+          }
           S0 += w;
-          S1 += wq;
-          R0 = fma(m, w, R0);
-          R1 = fma(m, wq, R1);
+          R0 = fma(T.m64[j], w, R0);
           if (j != (int)k) {
-            if (r < h) ++clt;
-            if (r >= hlo) {
-              if (band == 0) br0 = r;
-              else if (band == 1) br1 = r;
+            if (q < 1.0) ++clt;
+            if (q >= qlo) {
+              if (band == 0) bq0 = q;
+              else if (band == 1) bq1 = q;
               ++band;
             }
           }
@@ -321,8 +331,16 @@ struct SphEval64 {
   }
   __device__ __forceinline__ void operator()(const SphBufs& Wb, int count) {
     for (int s = 0; s < count; ++s) {
-      const float r2 = sph_r2_32(th, tl, Wb.sa[s], Wb.sb[s]);
-      if (r2 < hb2_32) W->list[cnt++][lane] = Wb.sj[s];
+      const float4 a = Wb.sa[s], b = Wb.sb[s];
+      const float tx = th.x - a.x, ty = th.y - a.y, tz = th.z - a.z;
+      const float nx = tx - sph_mi1(tx), ny = ty - sph_mi1(ty), nz = tz - sph_mi1(tz);  // rint, exact
+      const float dx = (tx - nx) + (tl.x - b.x), dy = (ty - ny) + (tl.y - b.y), dz = (tz - nz) + (tl.z - b.z);
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (r2 < hb2_32) {
+        W->list[cnt][lane] = Wb.sj[s];
+        W->img[cnt][lane] = (unsigned char)((int)nx + 1 + 3 * ((int)ny + 1) + 9 * ((int)nz + 1));
+        ++cnt;
+      }
       if (__any_sync(0xffffffffu, cnt == kSphList)) {
         __syncwarp();
         flush();
@@ -335,6 +353,7 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
   __shared__ int s_stack[kSphWarps][kSphStack];
   __shared__ int2 s_queue[kSphWarps][kSphQueue];
   __shared__ int s_list[kSphWarps][kSphList][32];
+  __shared__ unsigned char s_img[kSphWarps][kSphList][32];
   __shared__ int s_qoff[kSphWarps][kSphQueue + 1];
   __shared__ float4 s_sa[kSphWarps][32];
   __shared__ float4 s_sb[kSphWarps][32];
@@ -358,6 +377,7 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
   W.stack = s_stack[wib];
   W.queue = s_queue[wib];
   W.list = s_list[wib];
+  W.img = s_img[wib];
   W.qoff = s_qoff[wib];
   W.sa = s_sa[wib];
   W.sb = s_sb[wib];
@@ -402,6 +422,7 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
   // 2. FP32 Newton passes on ln h
   bool conv = !valid, fail = false;
   float blo = 0.f, bhi = 1e30f;
+  float S1_32 = 0.f, R1_32 = 0.f;  // the last FP32 pass's derivative sums
   uint32_t st = 0;
   for (int pass = 0; pass < kSphPass32 && __any_sync(0xffffffffu, !conv); ++pass) {
     const float Rl = conv ? 0.f : h;
@@ -413,9 +434,12 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
     ev.ih2 = 1.0f / (h * h);
     ev.S0 = 0.f;
     ev.S1 = 0.f;
+    ev.R1 = 0.f;
     st |= sph_gather(A, W, G, R, nodes_total, lane, ev);
     if (st) break;
     if (!conv) {
+      S1_32 = ev.S1;
+      R1_32 = ev.R1;
       const float N = (32.0f / 3.0f) * ev.S0;
       if (N < nngb) blo = h;
       else bhi = h;
@@ -446,6 +470,7 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
   bool done = !valid || fail;
   double hd = (double)h * L;
   double lo64 = 0.0, hi64 = 0.0;  // FP64 bracket (hi64 = 0: none yet)
+  double hprev = 0.0, Nprev = 0.0;  // the previous FP64 evaluation (hprev = 0: none)
   double h_out = NAN, rho_out = NAN;
   int ngb_out = -1;
   double xk[3];
@@ -461,15 +486,12 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
     ev.tl = tl;
 #pragma unroll
     for (int c = 0; c < 3; ++c) ev.x[c] = xk[c];
-    ev.h = hd;
-    ev.ih = 1.0 / hd;
-    ev.hlo = hd * (1.0 - 4e-6);
-    ev.hhi = hd * (1.0 + 4e-6);
-    const float hb = (float)(ev.hhi / L);
+    ev.ih2 = 1.0 / (hd * hd);
+    const float hb = (float)(hd * (1.0 + 4e-6) / L);
     ev.hb2_32 = done ? -1.f : hb * hb * 1.0001f + 1e-14f;
-    ev.S0 = ev.S1 = ev.R0 = ev.R1 = 0.0;
+    ev.S0 = ev.R0 = 0.0;
+    ev.bq0 = ev.bq1 = 0.0;
     ev.clt = ev.band = ev.cnt = 0;
-    ev.br0 = ev.br1 = 0.0;
     const float Rl = done ? 0.f : hb;
     const float R = __int_as_float((int)__reduce_max_sync(0xffffffffu, (unsigned)__float_as_int(Rl)));
     st |= sph_gather(A, W, G, R, nodes_total, lane, ev);
@@ -479,18 +501,27 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
       const double N = (32.0 / 3.0) * ev.S0;
       if (N < A.n_ngb) lo64 = hd;
       else hi64 = hd;
+      // Newton step with the derivative from the FP32 pass,
+      // dN/dh = -(32 / 3) sum q w'(q) / h; after a first FP64 evaluation,
+      // secant steps through the FP64 ones
       double hn;
-      if (ev.S1 < 0.0) hn = hd + (N - A.n_ngb) * hd / ((32.0 / 3.0) * ev.S1);
+      if (hprev > 0.0 && N != Nprev && hd != hprev) hn = hd - (N - A.n_ngb) * (hd - hprev) / (N - Nprev);
+      else if (S1_32 < 0.f) hn = hd + (N - A.n_ngb) * hd / ((32.0 / 3.0) * (double)S1_32);
       else hn = N >= A.n_ngb ? 0.5 * hd : 2.0 * hd;
+      hprev = hd;
+      Nprev = N;
       const bool small = fabs(hn - hd) <= 3e-6 * hd;
       if (!small && hi64 > 0.0 && lo64 > 0.0 && !(hn > lo64 && hn < hi64)) hn = 0.5 * (lo64 + hi64);
       if (small && (ev.band <= 2 || hn == hd)) {
         // the step stays inside the band, so only band neighbours can change
         // side between hd and hn
+        const double qn = hn / hd;
         int c = ev.clt;
-        if (ev.band >= 1) c += (int)(ev.br0 < hn) - (int)(ev.br0 < hd);
-        if (ev.band >= 2) c += (int)(ev.br1 < hn) - (int)(ev.br1 < hd);
-        const double R0f = ev.R0 - ev.R1 * (hn - hd) / hd;
+        if (ev.band >= 1) c += (int)(ev.bq0 < qn) - (int)(ev.bq0 < 1.0);
+        if (ev.band >= 2) c += (int)(ev.bq1 < qn) - (int)(ev.bq1 < 1.0);
+        // rho at hn to first order: d(sum m w)/dh = -(sum m q w'(q)) / h
+        const double R1 = (double)R1_32 * L * L;
+        const double R0f = ev.R0 - R1 * (hn - hd) / hd;
         h_out = hn;
         rho_out = 8.0 * R0f / (M_PI * hn * hn * hn);
         ngb_out = c;
