@@ -71,7 +71,7 @@ typedef enum og_precision {
 } og_precision;
 
 /* Tunables; the paper fixes none of them.  og_params_default() fills:
- * leaf_size 8, rcut_factor 4.5, node_capacity 0 (= 2n + 1024),
+ * leaf_size 16, rcut_factor 4.5, node_capacity 0 (= 2n + 1024),
  * max_walk_iters 0 (= 2^24 node visits per 32-particle group). */
 typedef struct og_params {
   int32_t leaf_size;       /* B: a node with more than B particles is split (1..32) */

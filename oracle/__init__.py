@@ -168,7 +168,7 @@ def direct(pos, mass, h, box, r_s, rcut, targets=None):
 class Tree:
     """Oracle octree (recursive octant subdivision of the integer cell grid)."""
 
-    def __init__(self, pos, mass, h, box: float = 1.0, leaf_size: int = 8):
+    def __init__(self, pos, mass, h, box: float = 1.0, leaf_size: int = 16):
         self._L = lib()
         self.pos = _pos(pos)
         self.n = self.pos.shape[0]

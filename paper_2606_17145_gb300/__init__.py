@@ -77,7 +77,7 @@ def _workspace(nbytes: int, device) -> torch.Tensor:
     return ws[off:off + max(int(nbytes), 256)]
 
 
-def params(leaf_size: int = 8, rcut_factor: float = 4.5, node_capacity: int = 0,
+def params(leaf_size: int = 16, rcut_factor: float = 4.5, node_capacity: int = 0,
            max_walk_iters: int = 0, deep_stack: int = 0) -> N.og_params:
     p = N.og_params()
     lib().og_params_default(C.byref(p))

@@ -29,7 +29,7 @@ extern "C" {
 void og_params_default(og_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
-  p->leaf_size = 8;
+  p->leaf_size = 16;
   p->rcut_factor = 4.5;
   p->node_capacity = 0;
   p->max_walk_iters = 0;

@@ -28,7 +28,7 @@ def test_params_and_sizes(L):
     from paper_2606_17145_gb300 import _native as N
     p = N.og_params()
     L.og_params_default(C.byref(p))
-    assert (p.leaf_size, p.rcut_factor, p.node_capacity, p.max_walk_iters) == (8, 4.5, 0, 0)
+    assert (p.leaf_size, p.rcut_factor, p.node_capacity, p.max_walk_iters) == (16, 4.5, 0, 0)
     assert L.og_keys_sort_ws_bytes(0) == 0
     assert L.og_keys_sort_ws_bytes(1000) >= 1000 * 12
     assert L.og_tree_bytes(1000, None) > L.og_tree_bytes(100, None) > 0
