@@ -92,33 +92,53 @@ __device__ __forceinline__ float pm_sinc(int k, int N) {
   return sinpif(t) / (3.14159265358979323846f * t);
 }
 
-// The R2C layout [N][N][N/2 + 1]: a block takes whole rows (ix, iy), its
-// threads the kz of the row, so no index is divided per coefficient.
-__global__ void k_pm_green(cufftComplex* __restrict__ C, int N, float inv_box, float two_pi_over_box, float r_s) {
+// The R2C layout [N][N][N/2 + 1], walked as one flat index: every thread
+// takes four coefficients a grid stride apart (four independent loads in
+// flight).  Both factors of the Green's function separate over the axes,
+// exp(-k^2 r_s^2) / S = prod_a exp(-q^2 k_a^2 r_s^2) / sinc^4(k_a / N), so each
+// block first tabulates T(k) = exp(-q^2 k^2 r_s^2) / sinc^4(k / N) for
+// k = 0 .. N / 2 in shared memory, and a coefficient costs three table
+// loads, two products and one reciprocal.
+constexpr int kGreenMaxHalf = 513;  // N / 2 + 1 for N <= 1024
+constexpr int kGreenUnroll = 4;
+__global__ void __launch_bounds__(256) k_pm_green(cufftComplex* __restrict__ C, int N, float inv_box,
+                                                  float two_pi_over_box, float r_s) {
+  __shared__ float Tk[kGreenMaxHalf];
   const int H = N / 2 + 1;
   const float pi = 3.14159265358979323846f;
   // 1 / D^3 (masses -> density) times 1 / N^3 (inverse transform) = 1 / L^3
   const float c0 = -4.0f * pi * (inv_box * inv_box * inv_box);
   const float q2 = two_pi_over_box * two_pi_over_box;
-  for (int row = blockIdx.x; row < N * N; row += gridDim.x) {
-    const int ix = row / N, iy = row - ix * N;
-    const int kx = ix <= N / 2 ? ix : ix - N;
-    const int ky = iy <= N / 2 ? iy : iy - N;
-    const float sxy = pm_sinc(kx, N) * pm_sinc(ky, N);
-    const int kxy = kx * kx + ky * ky;
-    cufftComplex* Crow = C + (int64_t)row * H;
-    for (int kz = threadIdx.x; kz < H; kz += blockDim.x) {
-      float g = 0.0f;
-      if (kxy != 0 || kz != 0) {
-        const float k2 = q2 * (float)(kxy + kz * kz);
-        const float s = sxy * pm_sinc(kz, N);
-        const float s2 = s * s;
-        g = c0 * expf(-k2 * r_s * r_s) / (k2 * s2 * s2);
+  for (int k = threadIdx.x; k < H; k += blockDim.x) {
+    const float s = pm_sinc(k, N);
+    const float s2 = s * s;
+    Tk[k] = expf(-q2 * (float)(k * k) * r_s * r_s) / (s2 * s2);
+  }
+  __syncthreads();
+  const int64_t total = (int64_t)N * N * H;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < total; i0 += kGreenUnroll * stride) {
+    cufftComplex v[kGreenUnroll];
+    float g[kGreenUnroll];
+#pragma unroll
+    for (int u = 0; u < kGreenUnroll; ++u) {
+      const int64_t i = i0 + u * stride;
+      g[u] = 0.0f;
+      if (i < total) {
+        v[u] = C[i];
+        const int64_t row = i / H;
+        const int kz = (int)(i - row * H);
+        const int ix = (int)(row / N), iy = (int)(row - (int64_t)ix * N);
+        const int kx = ix <= N / 2 ? ix : N - ix;  // |k|: T is even
+        const int ky = iy <= N / 2 ? iy : N - iy;
+        const int k2i = kx * kx + ky * ky + kz * kz;
+        if (k2i != 0) g[u] = c0 * Tk[kx] * Tk[ky] * Tk[kz] * __frcp_rn(q2 * (float)k2i);
       }
-      cufftComplex v = Crow[kz];
-      v.x *= g;
-      v.y *= g;
-      Crow[kz] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < kGreenUnroll; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < total) C[i] = make_float2(v[u].x * g[u], v[u].y * g[u]);
     }
   }
 }
@@ -289,8 +309,8 @@ og_status og_pm_accel(og_pm_plan* plan, const double* pos, const double* mass, i
       cufftExecR2C(plan->r2c, W.R, W.C) != CUFFT_SUCCESS)
     return OG_ECUDA;
   const int rows = N * N;
-  og::k_pm_green<<<(unsigned)(rows < (int)og::grid_cap(64) ? rows : (int)og::grid_cap(64)), 128, 0, s>>>(W.C, N, (float)(1.0 / box),
-                                                                              (float)(2.0 * M_PI / box), (float)r_s);
+  og::k_pm_green<<<(unsigned)(rows < (int)og::grid_cap(8) ? rows : (int)og::grid_cap(8)), 256, 0, s>>>(
+      W.C, N, (float)(1.0 / box), (float)(2.0 * M_PI / box), (float)r_s);
   if (cudaGetLastError() != cudaSuccess) return OG_ECUDA;
   if (cufftSetStream(plan->c2r, s) != CUFFT_SUCCESS || cufftSetWorkArea(plan->c2r, W.work) != CUFFT_SUCCESS ||
       cufftExecC2R(plan->c2r, W.C, W.R) != CUFFT_SUCCESS)
