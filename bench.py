@@ -533,29 +533,6 @@ def main():
     value = job_rate(interactions, ws, ms)
     pms = {k: sum(v) / len(v) for k, v in per.items()}
 
-    # FP64 walk on the same tree (comparison variant)
-    tr = state["tree"]
-    f64 = []
-    for _ in range(max(1, args.fp64_steps)):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        og.shortrange_accel(tr, w.r_s, args.theta, prec="fp64", check=False, ws=ws_acc, out=acc64, total=total64)
-        b.record()
-        torch.cuda.synchronize()
-        f64.append(a.elapsed_time(b))
-    f64_ms = sum(f64) / len(f64)
-    inter64 = int(total64.item())
-    code = og.poll_status(ws_acc)
-    if code != 0:
-        raise SystemExit(f"fp64 walk failed on the device: {L.og_status_str(code).decode()}")
-    # the FP32 accelerations of the same tree (the graph's last replay wrote acc)
-    og.shortrange_accel(tr, w.r_s, args.theta, ws=ws_acc, out=acc, total=total)
-    rel = (acc.double() - acc64).norm(dim=1) / acc64.norm(dim=1).clamp_min(1e-300)
-    fp32_vs_fp64 = {"rms_rel": float(rel.pow(2).mean().sqrt()), "max_rel": float(rel.max())}
-    acc_host = acc.double().cpu().numpy()
-
     # end to end through the public API with host buffers
     pos_h = pos.cpu().pin_memory()
     mass_h = mass.cpu().pin_memory()
@@ -612,16 +589,40 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = []
     e2e_steps = min(args.steps, 5)
-    for _ in range(e2e_steps):
+    with Clocks(local) as clk_e2e:
+        for _ in range(e2e_steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            e2e_step()
+            b.record()
+            torch.cuda.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_mean = max_over_ranks(sum(e2e_ms) / len(e2e_ms), ws, dev)
+
+    # FP64 walk on the same tree (comparison variant)
+    tr = state["tree"]
+    f64 = []
+    for _ in range(max(1, args.fp64_steps)):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
-        e2e_step()
+        og.shortrange_accel(tr, w.r_s, args.theta, prec="fp64", check=False, ws=ws_acc, out=acc64, total=total64)
         b.record()
         torch.cuda.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
-    e2e_mean = max_over_ranks(sum(e2e_ms) / len(e2e_ms), ws, dev)
+        f64.append(a.elapsed_time(b))
+    f64_ms = sum(f64) / len(f64)
+    inter64 = int(total64.item())
+    code = og.poll_status(ws_acc)
+    if code != 0:
+        raise SystemExit(f"fp64 walk failed on the device: {L.og_status_str(code).decode()}")
+    # the FP32 accelerations of the same tree (the graph's last replay wrote acc)
+    og.shortrange_accel(tr, w.r_s, args.theta, ws=ws_acc, out=acc, total=total)
+    rel = (acc.double() - acc64).norm(dim=1) / acc64.norm(dim=1).clamp_min(1e-300)
+    fp32_vs_fp64 = {"rms_rel": float(rel.pow(2).mean().sqrt()), "max_rel": float(rel.max())}
+    acc_host = acc.double().cpu().numpy()
 
     # roofline of the dominant kernel.  "peak" is the unit-count FP32 peak
     # (SMs x 128 FMA lanes x 2 flops x the maximum SM clock); the pipe rates
@@ -720,7 +721,8 @@ def main():
                    "launch": "CUDA graph replay of the whole step" if graph is not None else "stream launches"},
         "clocks": clocks,
         "e2e": {"value": job_rate(interactions, ws, e2e_mean), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean, "steps": e2e_steps},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean, "steps": e2e_steps,
+                "clocks": clk_e2e.summary()},
         "gpu_launches": per_step_launches * args.steps,
         "roofline": roofline,
         "interactions_per_step": interactions,
