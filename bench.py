@@ -357,10 +357,12 @@ def side_workload(og, L, name, dev, theta, steps, flush):
     t_fwd = timed_ms(lambda: og.shortrange_accel(tree, w.r_s, theta, check=False, ws=ws, out=acc, total=tot),
                      steps, flush)
     t_adj = timed_ms(lambda: og.shortrange_adjoint(tree, w.r_s, theta, wt, check=False, ws=wsa), steps, flush)
+    og.shortrange_accel_adjoint(tree, w.r_s, theta, wt, ws=wsa)
+    t_fu = timed_ms(lambda: og.shortrange_accel_adjoint(tree, w.r_s, theta, wt, check=False, ws=wsa), steps, flush)
     step = t_keys + t_tree + t_fwd + t_adj
     return {"workload": f"{name}: {WORKLOADS[name]}", "n": w.n, "interactions_per_step": inter,
             "ms": {"keys_sort": t_keys, "tree_build": t_tree, "accel_fp32": t_fwd, "adjoint_fp32": t_adj,
-                   "step": step},
+                   "step": step, "fused_fwd_adjoint": t_fu},
             "interactions_per_s": inter / (step * 1e-3), "fwd_interactions_per_s": inter / (t_fwd * 1e-3),
             "adj_interactions_per_s": inter / (t_adj * 1e-3), "fwd_particles_per_s": w.n / (t_fwd * 1e-3),
             "timed_steps": steps, "launch": "stream launches, L2 flushed"}
@@ -624,6 +626,26 @@ def main():
     fp32_vs_fp64 = {"rms_rel": float(rel.pow(2).mean().sqrt()), "max_rel": float(rel.max())}
     acc_host = acc.double().cpu().numpy()
 
+    # fused forward + adjoint (one walk; a loss whose weights are known before
+    # the forces): timed on the same tree, its accelerations checked against
+    # the separate forward walk's bit for bit
+    acc_fu = torch.empty_like(acc)
+    total_fu = torch.zeros(1, dtype=torch.int64, device=dev)
+    og.shortrange_accel_adjoint(tr, w.r_s, args.theta, wt, ws=ws_adj, out=acc_fu, total=total_fu, dpos=dpos,
+                                dmass=dmass)
+    fu_ms = timed_ms(lambda: og.shortrange_accel_adjoint(tr, w.r_s, args.theta, wt, check=False, ws=ws_adj,
+                                                         out=acc_fu, total=total_fu, dpos=dpos, dmass=dmass),
+                     max(1, min(args.steps, 3)), flush)
+    fu_ms = max_over_ranks(fu_ms, ws, dev)
+    fused = {"ms": fu_ms, "interactions_per_s": ws * interactions / (fu_ms * 1e-3),
+             "separate_ms": pms["accel_fp32"] + pms["adjoint_fp32"],
+             "speedup_vs_separate": (pms["accel_fp32"] + pms["adjoint_fp32"]) / fu_ms,
+             "same_acc_bits": bool(torch.equal(acc_fu.view(torch.int32), acc.view(torch.int32))),
+             "same_interactions": int(total_fu.item()) == interactions,
+             "what": "og_shortrange_accel_adjoint: the adjoint walk that also writes the accelerations, "
+                     "plus the push-down; L2 flushed"}
+    del acc_fu
+
     # roofline of the dominant kernel.  "peak" is the unit-count FP32 peak
     # (SMs x 128 FMA lanes x 2 flops x the maximum SM clock); the pipe rates
     # measured above give the "_measured" fractions and the MUFU and FP64 ones.
@@ -722,6 +744,7 @@ def main():
         "clocks": clocks,
         "e2e": {"value": job_rate(interactions, ws, e2e_mean), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_mean, "steps": e2e_steps,
+                "step_ms": [round(x, 2) for x in e2e_ms],
                 "clocks": clk_e2e.summary()},
         "gpu_launches": per_step_launches * args.steps,
         "roofline": roofline,
@@ -732,6 +755,7 @@ def main():
         "adj_interactions_per_s": ws * interactions / (pms["adjoint_fp32"] * 1e-3),
         "fwd_adj_particles_per_s": ws * n / ((pms["accel_fp32"] + pms["adjoint_fp32"]) * 1e-3),
         "breakdown_ms": pms,
+        "fused_fwd_adjoint": fused,
         "fp64": {"ms": f64_ms, "interactions_per_s": ws * inter64 / (f64_ms * 1e-3),
                  "same_interactions": inter64 == interactions,
                  "fp32_speedup": f64_ms / pms["accel_fp32"], "fp32_vs_fp64": fp32_vs_fp64},

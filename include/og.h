@@ -214,6 +214,32 @@ og_status og_shortrange_adjoint(const og_tree* t, double r_s, double theta, og_p
                                 og_stream stream);
 
 /*
+ * og_shortrange_accel_adjoint -- og_shortrange_accel (FP32_KAHAN) and
+ * og_shortrange_adjoint in one walk, for a loss L = sum_i w_i . a_i whose
+ * weights w are known before the forces (the paper's walk, Sec. 2, 3.1, and
+ * its adjoint as documented above).  Each pair's force factor F(r) serves
+ * both the forward term and the adjoint terms, so the traversal, staging and
+ * cut tests are done once.
+ *
+ * The walk's decisions, batches and summation order are those of the
+ * separate calls, so acc, n_interact and counts equal og_shortrange_accel's
+ * and dpos, dmass equal og_shortrange_adjoint's for the same tree.
+ *
+ * prec         OG_FP32_KAHAN only (OG_FP64: OG_ENOTIMPL)
+ * w            device, float[n][3] (original order)
+ * acc          device out, float[n][3], original order (required)
+ * n_interact   device out (optional, may be NULL): uint64 total interactions
+ * counts       device out (optional, may be NULL): int32[n], original order
+ * dpos         device out, double[n][3]; dmass device out, double[n]
+ * ws, ws_bytes device workspace of at least og_adjoint_ws_bytes(t, 1)
+ * Status and errors as for og_shortrange_adjoint (read with og_poll_status
+ * on ws).
+ */
+og_status og_shortrange_accel_adjoint(const og_tree* t, double r_s, double theta, og_precision prec, const float* w,
+                                      float* acc, uint64_t* n_interact, int32_t* counts, double* dpos,
+                                      double* dmass, void* ws, size_t ws_bytes, og_stream stream);
+
+/*
  * og_shortrange_accel_range / og_shortrange_adjoint_range -- the same walks
  * over the walk groups [g_begin, g_end) only, i.e. over the targets with
  * sorted indices [32 g_begin, min(32 g_end, n)): a contiguous range of

@@ -234,6 +234,36 @@ def shortrange_adjoint(tree: Tree, r_s: float, theta: float, w: torch.Tensor, st
     return dpos, dmass
 
 
+def shortrange_accel_adjoint(tree: Tree, r_s: float, theta: float, w: torch.Tensor, counts: bool = False,
+                             stream=None, check: bool = True, ws: torch.Tensor | None = None,
+                             out: torch.Tensor | None = None, total: torch.Tensor | None = None,
+                             dpos: torch.Tensor | None = None, dmass: torch.Tensor | None = None):
+    """Forward and adjoint in one walk (og_shortrange_accel_adjoint), for
+    L = sum w . a with w known in advance.  Returns (acc, total, counts, dpos,
+    dmass), each as from shortrange_accel / shortrange_adjoint."""
+    _cuda(w, torch.float32, (3,), "w")
+    L = lib()
+    dev = tree.mem.device
+    n = tree.n
+    if out is None:
+        out = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    if total is None:
+        total = torch.zeros(1, dtype=torch.int64, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev) if counts else None
+    if ws is None:
+        ws = _workspace(L.og_adjoint_ws_bytes(C.byref(tree.header), 1), dev)
+    if dpos is None:
+        dpos = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    if dmass is None:
+        dmass = torch.empty(n, dtype=torch.float64, device=dev)
+    _check(L.og_shortrange_accel_adjoint(C.byref(tree.header), float(r_s), float(theta), N.OG_FP32_KAHAN, _ptr(w),
+                                         _ptr(out), _ptr(total), _ptr(cnt), _ptr(dpos), _ptr(dmass), _ptr(ws),
+                                         ws.numel(), _stream(stream)), "og_shortrange_accel_adjoint")
+    if check:
+        _check(poll_status(ws, stream), "og_shortrange_accel_adjoint (device)")
+    return out, total, cnt, dpos, dmass
+
+
 class PMPlan:
     """cuFFT plans for an N^3 long-range mesh (og_pm_plan_create); frees them when collected."""
 

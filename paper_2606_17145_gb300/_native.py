@@ -48,6 +48,9 @@ SIGNATURES = {
     "og_shortrange_adjoint_range": (C.c_int, [C.POINTER(og_tree), C.c_double, C.c_double, C.c_int, C.c_void_p,
                                               C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                               C.c_size_t, C.c_void_p]),
+    "og_shortrange_accel_adjoint": (C.c_int, [C.POINTER(og_tree), C.c_double, C.c_double, C.c_int, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_size_t, C.c_void_p]),
     "og_keys_sort_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "og_poll_status": (C.c_int, [C.c_void_p, C.c_void_p]),
     "og_tree_node_count": (C.c_int64, [C.POINTER(og_tree), C.c_void_p]),

@@ -203,9 +203,12 @@ og_status og_shortrange_adjoint(const og_tree* t, double r_s, double theta, og_p
                                      ws_bytes, stream);
 }
 
-og_status og_shortrange_adjoint_range(const og_tree* t, double r_s, double theta, og_precision prec, const float* w,
-                                      int64_t g_begin, int64_t g_end, double* dpos, double* dmass,
-                                      int recompute_lists, void* ws, size_t ws_bytes, og_stream stream) {
+// The adjoint walk of groups [g_begin, g_end) and the push-down; with acc
+// set, the same walk also writes the forward accelerations (fused).
+static og_status adjoint_walk(const og_tree* t, double r_s, double theta, og_precision prec, const float* w,
+                              int64_t g_begin, int64_t g_end, float* acc, uint64_t* n_interact, int32_t* counts,
+                              double* dpos, double* dmass, int recompute_lists, void* ws, size_t ws_bytes,
+                              og_stream stream) {
   if (!w || !dpos || !dmass || !ws) return OG_EINVAL;
   if (prec != OG_FP32_KAHAN) return prec == OG_FP64 ? OG_ENOTIMPL : OG_EINVAL;
   if (recompute_lists != 1) return recompute_lists == 0 ? OG_ENOTIMPL : OG_EINVAL;
@@ -231,10 +234,35 @@ og_status og_shortrange_adjoint_range(const og_tree* t, double r_s, double theta
   A.Gp = W.Gp;
   A.Sp = W.Sp;
   A.tgt = W.tgt;
-  e = launch_walk(A, (int)prec, true, s);
+  if (acc) {
+    A.accf = acc;
+    A.counts = counts;
+    A.total = reinterpret_cast<unsigned long long*>(n_interact);
+    if (n_interact) {
+      e = cudaMemsetAsync(n_interact, 0, sizeof(uint64_t), s);
+      if (e != cudaSuccess) return OG_ECUDA;
+    }
+  }
+  e = launch_walk(A, (int)prec, true, s, acc != nullptr);
   if (e != cudaSuccess) return OG_ECUDA;
   TreeDev T = tree_view(t);
   return cuda_status(launch_adjoint_push(T, W, t->box, dpos, dmass, s));
+}
+
+og_status og_shortrange_adjoint_range(const og_tree* t, double r_s, double theta, og_precision prec, const float* w,
+                                      int64_t g_begin, int64_t g_end, double* dpos, double* dmass,
+                                      int recompute_lists, void* ws, size_t ws_bytes, og_stream stream) {
+  return adjoint_walk(t, r_s, theta, prec, w, g_begin, g_end, nullptr, nullptr, nullptr, dpos, dmass,
+                      recompute_lists, ws, ws_bytes, stream);
+}
+
+og_status og_shortrange_accel_adjoint(const og_tree* t, double r_s, double theta, og_precision prec, const float* w,
+                                      float* acc, uint64_t* n_interact, int32_t* counts, double* dpos,
+                                      double* dmass, void* ws, size_t ws_bytes, og_stream stream) {
+  if (!t) return OG_ETREE;
+  if (!acc) return OG_EINVAL;
+  return adjoint_walk(t, r_s, theta, prec, w, 0, t->n_groups, acc, n_interact, counts, dpos, dmass, 1, ws,
+                      ws_bytes, stream);
 }
 
 og_status og_poll_status(const void* buf, og_stream stream) {

@@ -338,7 +338,9 @@ inline unsigned grid_cap(int per_sm) {
 cudaError_t launch_keys_sort(const double* pos, int64_t n, double L, uint64_t* keys_out, int32_t* order_out,
                              const SortWs& W, cudaStream_t s);
 cudaError_t launch_tree_build(const BuildArgs& A, cudaStream_t s);
-cudaError_t launch_walk(const WalkArgs& A, int prec, bool adjoint, cudaStream_t s);
+// fused (with adjoint): the adjoint walk that also writes accf, counts and
+// the interaction total from the same pair evaluations
+cudaError_t launch_walk(const WalkArgs& A, int prec, bool adjoint, cudaStream_t s, bool fused = false);
 cudaError_t launch_adjoint_push(const TreeDev& T, const AdjWs& W, double L, double* dpos, double* dmass,
                                 cudaStream_t s);
 cudaError_t launch_copy_nodes(const TreeDev& T, int64_t m, int32_t* level, int32_t* first, int32_t* count,

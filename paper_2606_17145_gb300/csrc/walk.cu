@@ -423,8 +423,12 @@ template <> struct Term<true> { double x, y, z; float w; };
 // FP64 decisions, FP64 pair arithmetic with CUDA's erfc / exp, plain double
 // sums).  All share the traversal, the box test, the FP32 cut filter (a
 // conservative superset of the pairs inside the cut) and the compaction.
-template <bool ADJ, bool F64>
+// FUSED (with ADJ): the adjoint walk that also writes the forward
+// accelerations, each pair's force factor serving both (one traversal for a
+// loss whose weights are known before the walk).
+template <bool ADJ, bool F64, bool FUSED = false>
 struct LaneFP {
+  static_assert(!FUSED || (ADJ && !F64), "the fused walk is the FP32 adjoint plus the forward sums");
   // per-warp data that lives through the whole walk
   struct Smem {
     float4 tA[kGroup];    // targets: hi part, h^2
@@ -434,6 +438,7 @@ struct LaneFP {
     uint32_t smask[ADJ ? kSlots : 1];  // adjoint: the lanes whose listed pair has this slot
     int self[kGroup];     // staged slot holding the target itself, or -1
     typename std::conditional<F64, double3, float4>::type Ps[kGroup];  // each target's sum over the batch
+    float4 Pf[FUSED ? kGroup : 1];  // fused: each target's forward sum over the batch
     int fneg[kGroup];     // listed pairs of the batch found outside the exact cut
   };
   // per-batch staging (dead between evaluations; shares memory with the
@@ -461,6 +466,7 @@ struct LaneFP {
   float xr[3], sr;    // position relative to the group centre and its square (filter)
   float P[3];         // partial sum since the last fold
   float S[3], C[3];   // Kahan total and compensation
+  float Pf[3], Sf[3], Cf[3];  // fused: the forward sums likewise
   double a64[3];      // FP64 variant: plain double sums
   int nint;
   float4 gs;          // adjoint: this lane's slot, source-side sums (G, S) over the batch
@@ -483,7 +489,8 @@ struct LaneFP {
     xr[2] = (a.z - G.cz) + b.z;
     sr = fmaf(xr[0], xr[0], fmaf(xr[1], xr[1], xr[2] * xr[2]));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { P[c] = 0.f; S[c] = 0.f; C[c] = 0.f; }
+    for (int c = 0; c < 3; ++c) { P[c] = 0.f; S[c] = 0.f; C[c] = 0.f; Pf[c] = 0.f; Sf[c] = 0.f; Cf[c] = 0.f; }
+    if constexpr (FUSED) M.Pf[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (ADJ) {
       float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
       if (v) {
@@ -626,6 +633,10 @@ struct LaneFP {
     for (int c = 0; c < 3; ++c) {
       kahan_add(S[c], C[c], P[c]);
       P[c] = 0.f;
+      if constexpr (FUSED) {
+        kahan_add(Sf[c], Cf[c], Pf[c]);
+        Pf[c] = 0.f;
+      }
     }
   }
 
@@ -633,7 +644,8 @@ struct LaneFP {
   // the interaction (target-side term, hit flag).  In the adjoint the
   // source-side terms go to sg.
   __device__ __forceinline__ float4 pair_eval(const WalkArgs& A, const Stage& St, const Smem& M, int i, int s,
-                                              int64_t gbase, float4& sg) const {
+                                              int64_t gbase, float4& sg, float3& fw) const {
+    fw = make_float3(0.f, 0.f, 0.f);
     const float4 ta = M.tA[i], tb = M.tB[i];
     const float4 a = St.sa[s], b = St.sb[s];
     const int2 c = St.sc[s];
@@ -666,6 +678,10 @@ struct LaneFP {
       const float j1 = -fmaf(F, w.y, qq * dv[1]);
       const float j2 = -fmaf(F, w.z, qq * dv[2]);
       sg = make_float4(j0, j1, j2, -F * dw);
+      if constexpr (FUSED) {
+        const float sc = -a.w * F;
+        fw = make_float3(sc * dv[0], sc * dv[1], sc * dv[2]);
+      }
       return make_float4(a.w * j0, a.w * j1, a.w * j2, 1.f);
     }
   }
@@ -783,6 +799,7 @@ struct LaneFP {
           r.x = r.y = r.z = 0;
           r.w = 0.f;
           float4 sg = make_float4(0.f, 0.f, 0.f, 0.f);
+          float3 fw = make_float3(0.f, 0.f, 0.f);
           if (hv) {
             const int e = W.list[p];
             i = e >> 5;
@@ -790,7 +807,7 @@ struct LaneFP {
             if constexpr (F64) {
               r = pair_eval64(A, St, i, hb + slot, gbase);
             } else {
-              const float4 rr = pair_eval(A, St, M, i, hb + slot, gbase, sg);
+              const float4 rr = pair_eval(A, St, M, i, hb + slot, gbase, sg, fw);
               r.x = rr.x;
               r.y = rr.y;
               r.z = rr.z;
@@ -814,6 +831,16 @@ struct LaneFP {
               r.y += y1;
               r.z += y2;
             }
+            if constexpr (FUSED) {
+              const float f0 = __shfl_up_sync(0xffffffffu, fw.x, d);
+              const float f1 = __shfl_up_sync(0xffffffffu, fw.y, d);
+              const float f2 = __shfl_up_sync(0xffffffffu, fw.z, d);
+              if (lane - d >= first) {
+                fw.x += f0;
+                fw.y += f1;
+                fw.z += f2;
+              }
+            }
           }
           if (hv && p == min(min(oi + ci, we), p0 + 32) - 1) {
             auto a = M.Ps[i];
@@ -821,6 +848,13 @@ struct LaneFP {
             a.y += r.y;
             a.z += r.z;
             M.Ps[i] = a;
+            if constexpr (FUSED) {
+              float4 b = M.Pf[i];
+              b.x += fw.x;
+              b.y += fw.y;
+              b.z += fw.z;
+              M.Pf[i] = b;
+            }
           }
           if (ADJ) {
             // source-side terms: each listed pair's term goes to shared
@@ -868,6 +902,13 @@ struct LaneFP {
         P[1] += ps.y;
         P[2] += ps.z;
         M.Ps[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (FUSED) {
+          const float4 pf = M.Pf[lane];
+          Pf[0] += pf.x;
+          Pf[1] += pf.y;
+          Pf[2] += pf.z;
+          M.Pf[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
       nint -= M.fneg[lane];
       M.fneg[lane] = 0;
@@ -905,6 +946,11 @@ struct LaneFP {
     } else {
 #pragma unroll
       for (int c = 0; c < 3; ++c) A.tgt[3 * k + c] = (double)S[c] - (double)C[c];
+      if constexpr (FUSED) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A.accf[3 * (int64_t)i + c] = Sf[c] - Cf[c];
+        if (A.counts) A.counts[i] = nint;
+      }
     }
   }
 };
@@ -912,6 +958,7 @@ struct LaneFP {
 template <bool ADJ>
 using LaneF32 = LaneFP<ADJ, false>;
 using LaneF64 = LaneFP<false, true>;
+using LaneFused = LaneFP<true, false, true>;
 
 // ------------------------------------------------------------------ traversal
 
@@ -1209,10 +1256,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   }
 }
 
-cudaError_t launch_walk(const WalkArgs& A, int prec, bool adjoint, cudaStream_t s) {
+cudaError_t launch_walk(const WalkArgs& A, int prec, bool adjoint, cudaStream_t s, bool fused) {
   const int64_t blocks = (A.g_end - A.g_begin + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (blocks <= 0) return cudaSuccess;
-  if (adjoint) k_walk<LaneF32<true>><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(A);
+  if (fused) k_walk<LaneFused><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(A);
+  else if (adjoint) k_walk<LaneF32<true>><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(A);
   else if (prec == OG_FP64) k_walk<LaneF64><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(A);
   else k_walk<LaneF32<false>><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(A);
   return cudaGetLastError();
