@@ -20,21 +20,22 @@
 //   2. FP32 passes: Newton steps on ln h, ln N_eff(h) = ln N_ngb, with
 //      d ln N_eff / d ln h = -sum q w'(q) / sum w(q), a bracket of the root kept
 //      from every evaluation (a step leaving it is replaced by the bracket's
-//      geometric mean) and steps clamped to a factor 2; until |d ln h| < 1e-5.
+//      geometric mean) and steps clamped to a factor 2, until a step below
+//      1e-3 (taken, leaving ~1e-7).
 //      Distances come from the split-float positions (FP64 accuracy rounded
 //      to FP32).
 //   3. FP64 pass: each lane lists its candidates within h (1 + 4e-6) (FP32
 //      test with a margin) and their periodic image in shared memory, and the
 //      lists are evaluated lane-parallel in FP64 (the FP64 pipe is too narrow
-//      for lane-masked evaluation of every group candidate).  Only sum w and
-//      sum m w are taken in FP64.  One Newton step from the FP32 root gives
-//      h, with the derivative of the last FP32 pass (it scales a step below
-//      3e-6 h); the density at that h follows to first order from the sums
-//      at the evaluated h (neglected term ~1e-11 relative, the first-order
-//      term's derivative again from FP32); the neighbour count at the new h is the
-//      count at the evaluated one corrected by the neighbours within 4e-6 h
-//      of it (their distances are kept, up to two; with more the pass is
-//      repeated at the new h).
+//      for lane-masked evaluation of every group candidate).  Sum w and sum
+//      m w are taken in FP64, sum q w'(q) and sum m q w'(q) in FP32 (they
+//      only scale a step below 3e-6 h).  One Newton step from the FP32 root
+//      with the derivative at that root gives h; the density at that h
+//      follows to first order from the sums at the evaluated h (neglected
+//      term ~1e-11 relative); the neighbour count at the new h is the count
+//      at the evaluated one corrected by the neighbours within 4e-6 h of it
+//      (their distances are kept, up to two; with more, or a larger step,
+//      the pass is repeated at the new h).
 // Every loop is bounded (node-visit cap, pass caps, the stack bound); a
 // particle whose h does not converge below half the box gets NaN / -1 and
 // sets a status bit.
@@ -54,6 +55,11 @@ constexpr int kSphQueueNeed = 32;     // a step queues at most one leaf per popp
 constexpr int kSphList = 32;          // FP64 pass: listed candidates per lane before a flush
 constexpr int kSphPass32 = 32;        // FP32 Newton passes at most
 constexpr int kSphPass64 = 8;         // FP64 passes at most
+// FP32 passes stop once a Newton step on ln h is below this; the step is
+// still taken, and Newton's quadratic convergence leaves an error of about
+// (f''/2f') dl^2 ~ 1e-7 (f = ln N_eff(ln h), f' ~ 3), well inside the
+// 3e-6 h that the FP64 pass accepts in one evaluation.
+constexpr float kSphConv32 = 1e-3f;
 
 struct SphArgs {
   TreeDev T;
@@ -72,37 +78,6 @@ __device__ __forceinline__ float sph_mi1(float t) {
   return __fadd_rn(t, -r);
 }
 
-// w(q) and q w'(q) of the cubic spline (w = 1 - 6 q^2 + 6 q^3 for q <= 1/2,
-// 2 (1 - q)^3 for 1/2 < q < 1, 0 beyond).
-__device__ __forceinline__ void spline_w32(float q, float& w, float& wq) {
-  if (q <= 0.5f) {
-    const float q2 = q * q;
-    w = fmaf(q2, 6.0f * q - 6.0f, 1.0f);
-    wq = q2 * (18.0f * q - 12.0f);
-  } else if (q < 1.0f) {
-    const float t = 1.0f - q;
-    w = 2.0f * t * t * t;
-    wq = -6.0f * q * t * t;
-  } else {
-    w = 0.0f;
-    wq = 0.0f;
-  }
-}
-__device__ __forceinline__ void spline_w64(double q, double& w, double& wq) {
-  if (q <= 0.5) {
-    const double q2 = q * q;
-    w = fma(q2, 6.0 * q - 6.0, 1.0);
-    wq = q2 * (18.0 * q - 12.0);
-  } else if (q < 1.0) {
-    const double t = 1.0 - q;
-    w = 2.0 * t * t * t;
-    wq = -6.0 * q * t * t;
-  } else {
-    w = 0.0;
-    wq = 0.0;
-  }
-}
-
 struct SphBufs {
   int* stack;
   int2* queue;
@@ -117,6 +92,28 @@ struct SphBufs {
 struct SphGroup {
   float cx, cy, cz, ex, ey, ez;  // group box centre and half extents (box units, padded)
 };
+
+// Bounding box of the active lanes' targets (hi parts, box units, which are
+// non-negative and order like their bit patterns), padded by 1e-6 for the lo
+// parts and rounding.  A pass gathers around the lanes it still has to
+// serve, so a group whose other lanes have converged reaches fewer leaves.
+__device__ __forceinline__ SphGroup active_box(const float3& th, bool act) {
+  const uint32_t inf = 0x7f800000u;
+  const float lx = __uint_as_float(__reduce_min_sync(0xffffffffu, act ? __float_as_uint(th.x) : inf));
+  const float ly = __uint_as_float(__reduce_min_sync(0xffffffffu, act ? __float_as_uint(th.y) : inf));
+  const float lz = __uint_as_float(__reduce_min_sync(0xffffffffu, act ? __float_as_uint(th.z) : inf));
+  const float hx = __uint_as_float(__reduce_max_sync(0xffffffffu, act ? __float_as_uint(th.x) : 0u));
+  const float hy = __uint_as_float(__reduce_max_sync(0xffffffffu, act ? __float_as_uint(th.y) : 0u));
+  const float hz = __uint_as_float(__reduce_max_sync(0xffffffffu, act ? __float_as_uint(th.z) : 0u));
+  SphGroup G;
+  G.cx = 0.5f * (lx + hx);
+  G.cy = 0.5f * (ly + hy);
+  G.cz = 0.5f * (lz + hz);
+  G.ex = 0.5f * (hx - lx) * 1.0001f + 1e-6f;
+  G.ey = 0.5f * (hy - ly) * 1.0001f + 1e-6f;
+  G.ez = 0.5f * (hz - lz) * 1.0001f + 1e-6f;
+  return G;
+}
 
 // One gather: every leaf whose cube comes within R (box units) of the group
 // box is passed to eval(first, count), in batches.  Warp-uniform control
@@ -210,21 +207,37 @@ __device__ uint32_t sph_gather(const SphArgs& A, const SphBufs& W, const SphGrou
       __syncwarp();
       // stage the candidates 32 at a time (one coalesced load per lane) and
       // let every lane evaluate them from shared memory
+      // and let every lane evaluate them from shared memory; a particle
+      // beyond R of the box is not staged (the leaf's cube reached the
+      // sphere, the particle does not)
       for (int s0 = 0; s0 < run; s0 += 32) {
         const int slot = s0 + lane;
+        bool stage = false;
+        float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
+        int j = 0;
         if (slot < run) {
           int lo = 0, hi = nq - 1;
           while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (W.qoff[mid] <= slot) lo = mid; else hi = mid - 1;
           }
-          const int j = W.queue[lo].x + (slot - W.qoff[lo]);
-          W.sa[lane] = T.pA[j];
-          W.sb[lane] = T.pB[j];
-          W.sj[lane] = j;
+          j = W.queue[lo].x + (slot - W.qoff[lo]);
+          pa = T.pA[j];
+          pb = T.pB[j];
+          const float gx = fmaxf(fabsf(sph_mi1(pa.x - G.cx)) - G.ex, 0.f);
+          const float gy = fmaxf(fabsf(sph_mi1(pa.y - G.cy)) - G.ey, 0.f);
+          const float gz = fmaxf(fabsf(sph_mi1(pa.z - G.cz)) - G.ez, 0.f);
+          stage = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= R2;
+        }
+        const uint32_t sm = __ballot_sync(0xffffffffu, stage);
+        if (stage) {
+          const int at = __popc(sm & lt);
+          W.sa[at] = pa;
+          W.sb[at] = pb;
+          W.sj[at] = j;
         }
         __syncwarp();
-        eval(W, min(32, run - s0));
+        if (sm) eval(W, __popc(sm));
         __syncwarp();
       }
       nq = 0;
@@ -243,22 +256,26 @@ __device__ __forceinline__ float sph_r2_32(const float3& th, const float3& tl, c
   return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
-// FP32 pass: sums of w(q), q w'(q) and m q w'(q) over the particles within h.
+// FP32 pass: sums of w(q) and q w'(q) over the particles within h.
 struct SphEval32 {
   float3 th, tl;
-  float h2, ih2;  // h^2, 1 / h^2 (box units)
-  float S0, S1, R1;  // R1 in units of m / L^2 (the staged mass)
+  float ih2;  // 1 / h^2 (box units)
+  float S0, S1;
+  // Branch-free: w(q) = 2 u^3 - 8 v^3 and q w'(q) = q (24 v^2 - 6 u^2) with
+  // u = max(1 - q, 0), v = max(1/2 - q, 0) (both zero beyond the support),
+  // so the warp does not diverge on which lanes hold the candidate.
   __device__ __forceinline__ void operator()(const SphBufs& W, int count) {
+#pragma unroll 2
     for (int s = 0; s < count; ++s) {
       const float4 a = W.sa[s];
       const float r2 = sph_r2_32(th, tl, a, W.sb[s]);
-      if (r2 < h2) {
-        float w, wq;
-        spline_w32(sqrtf(r2 * ih2), w, wq);
-        S0 += w;
-        S1 += wq;
-        R1 = fmaf(a.w, wq, R1);
-      }
+      const float x = fmaxf(r2 * ih2, 1e-30f);
+      const float q = x * rsqrtf(x);
+      const float u = fmaxf(1.0f - q, 0.0f), v = fmaxf(0.5f - q, 0.0f);
+      const float u2 = u * u, v2 = v * v;
+      S0 += fmaf(2.0f * u2, u, -8.0f * v2 * v);
+      const float wq = q * fmaf(24.0f, v2, -6.0f * u2);
+      S1 += wq;
     }
   }
 };
@@ -267,7 +284,8 @@ struct SphEval32 {
 // list with their periodic image; a full list anywhere in the warp is
 // flushed, i.e. every lane evaluates its listed candidates in FP64.  Only the
 // sums that set h and rho to 1e-12 are taken in FP64 (sum w, sum m w); the
-// derivatives, which scale a step below 3e-6 h, come from the FP32 pass.
+// derivatives, which scale a step below 3e-6 h, are FP32 sums of the same
+// neighbours.
 struct SphEval64 {
   const SphArgs* A;
   const SphBufs* W;
@@ -278,6 +296,7 @@ struct SphEval64 {
   double x[3];         // target position (physical, wrapped)
   double ih2;          // 1 / h^2 (physical)
   double S0, R0;
+  float S1, R1;        // sum q w'(q) and sum m q w'(q) at this h (the step's derivative)
   double bq0, bq1;     // q = r / h of the first two neighbours in the band
   int clt, band, cnt;
   __device__ __forceinline__ void flush() {
@@ -315,6 +334,12 @@ struct SphEval64 {
           }
           S0 += w;
           R0 = fma(T.m64[j], w, R0);
+          if (q < 1.0) {
+            const float qf = (float)q, uf = 1.0f - qf;
+            const float wq = qf <= 0.5f ? qf * qf * fmaf(18.0f, qf, -12.0f) : -6.0f * qf * uf * uf;
+            S1 += wq;
+            R1 = fmaf((float)T.m64[j], wq, R1);
+          }
           if (j != (int)k) {
             if (q < 1.0) ++clt;
             if (q >= qlo) {
@@ -389,16 +414,6 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
   const int64_t k = g * kGroup + lane;
   const bool valid = k < T.n;
   const int64_t kc = valid ? k : 0;
-  SphGroup G;
-  {
-    const float4 lo = T.gbox[2 * g], hi = T.gbox[2 * g + 1];
-    G.cx = 0.5f * (lo.x + hi.x);
-    G.cy = 0.5f * (lo.y + hi.y);
-    G.cz = 0.5f * (lo.z + hi.z);
-    G.ex = 0.5f * (hi.x - lo.x) * 1.0001f + 1e-7f;
-    G.ey = 0.5f * (hi.y - lo.y) * 1.0001f + 1e-7f;
-    G.ez = 0.5f * (hi.z - lo.z) * 1.0001f + 1e-7f;
-  }
   const float4 pa = T.pA[kc], pb = T.pB[kc];
   const float3 th = make_float3(pa.x, pa.y, pa.z), tl = make_float3(pb.x, pb.y, pb.z);
   const float nngb = (float)A.n_ngb;
@@ -422,7 +437,6 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
   // 2. FP32 Newton passes on ln h
   bool conv = !valid, fail = false;
   float blo = 0.f, bhi = 1e30f;
-  float S1_32 = 0.f, R1_32 = 0.f;  // the last FP32 pass's derivative sums
   uint32_t st = 0;
   for (int pass = 0; pass < kSphPass32 && __any_sync(0xffffffffu, !conv); ++pass) {
     const float Rl = conv ? 0.f : h;
@@ -430,16 +444,12 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
     SphEval32 ev;
     ev.th = th;
     ev.tl = tl;
-    ev.h2 = h * h;
     ev.ih2 = 1.0f / (h * h);
     ev.S0 = 0.f;
     ev.S1 = 0.f;
-    ev.R1 = 0.f;
-    st |= sph_gather(A, W, G, R, nodes_total, lane, ev);
+    st |= sph_gather(A, W, active_box(th, !conv), R, nodes_total, lane, ev);
     if (st) break;
     if (!conv) {
-      S1_32 = ev.S1;
-      R1_32 = ev.R1;
       const float N = (32.0f / 3.0f) * ev.S0;
       if (N < nngb) blo = h;
       else bhi = h;
@@ -450,7 +460,7 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
       if (h >= 0.5f && N < nngb) {
         fail = true;  // no root below half the box
         conv = true;
-      } else if (fabsf(dl) < 1e-5f) {
+      } else if (fabsf(dl) < kSphConv32) {
         // converged: take the Newton step itself (it may round to h, which
         // is a bracket end by now, so it is not tested against the bracket)
         h = fminf(h * __expf(dl), 0.5f);
@@ -470,7 +480,6 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
   bool done = !valid || fail;
   double hd = (double)h * L;
   double lo64 = 0.0, hi64 = 0.0;  // FP64 bracket (hi64 = 0: none yet)
-  double hprev = 0.0, Nprev = 0.0;  // the previous FP64 evaluation (hprev = 0: none)
   double h_out = NAN, rho_out = NAN;
   int ngb_out = -1;
   double xk[3];
@@ -490,29 +499,29 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
     const float hb = (float)(hd * (1.0 + 4e-6) / L);
     ev.hb2_32 = done ? -1.f : hb * hb * 1.0001f + 1e-14f;
     ev.S0 = ev.R0 = 0.0;
+    ev.S1 = ev.R1 = 0.f;
     ev.bq0 = ev.bq1 = 0.0;
     ev.clt = ev.band = ev.cnt = 0;
     const float Rl = done ? 0.f : hb;
     const float R = __int_as_float((int)__reduce_max_sync(0xffffffffu, (unsigned)__float_as_int(Rl)));
-    st |= sph_gather(A, W, G, R, nodes_total, lane, ev);
+    st |= sph_gather(A, W, active_box(th, !done), R, nodes_total, lane, ev);
     if (st) break;
     ev.flush();
     if (!done) {
       const double N = (32.0 / 3.0) * ev.S0;
       if (N < A.n_ngb) lo64 = hd;
       else hi64 = hd;
-      // Newton step with the derivative from the FP32 pass,
-      // dN/dh = -(32 / 3) sum q w'(q) / h; after a first FP64 evaluation,
-      // secant steps through the FP64 ones
+      // Newton step, dN/dh = -(32 / 3) sum q w'(q) / h taken at hd (FP32
+      // terms: the derivative only scales a step below 3e-6 h)
       double hn;
-      if (hprev > 0.0 && N != Nprev && hd != hprev) hn = hd - (N - A.n_ngb) * (hd - hprev) / (N - Nprev);
-      else if (S1_32 < 0.f) hn = hd + (N - A.n_ngb) * hd / ((32.0 / 3.0) * (double)S1_32);
+      if (ev.S1 < 0.f) hn = hd + (N - A.n_ngb) * hd / ((32.0 / 3.0) * (double)ev.S1);
       else hn = N >= A.n_ngb ? 0.5 * hd : 2.0 * hd;
-      hprev = hd;
-      Nprev = N;
       const bool small = fabs(hn - hd) <= 3e-6 * hd;
       if (!small && hi64 > 0.0 && lo64 > 0.0 && !(hn > lo64 && hn < hi64)) hn = 0.5 * (lo64 + hi64);
-      if (small && (ev.band <= 2 || hn == hd)) {
+      // with more than two band neighbours (their distances are not kept)
+      // the step must be at the FP64 resolution: no neighbour then lies
+      // between hd and hn short of an exact tie
+      if (small && (ev.band <= 2 || fabs(hn - hd) <= 1e-12 * hd)) {
         // the step stays inside the band, so only band neighbours can change
         // side between hd and hn
         const double qn = hn / hd;
@@ -520,8 +529,7 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
         if (ev.band >= 1) c += (int)(ev.bq0 < qn) - (int)(ev.bq0 < 1.0);
         if (ev.band >= 2) c += (int)(ev.bq1 < qn) - (int)(ev.bq1 < 1.0);
         // rho at hn to first order: d(sum m w)/dh = -(sum m q w'(q)) / h
-        const double R1 = (double)R1_32 * L * L;
-        const double R0f = ev.R0 - R1 * (hn - hd) / hd;
+        const double R0f = ev.R0 - (double)ev.R1 * (hn - hd) / hd;
         h_out = hn;
         rho_out = 8.0 * R0f / (M_PI * hn * hn * hn);
         ngb_out = c;
