@@ -24,18 +24,19 @@
 //      1e-3 (taken, leaving ~1e-7).
 //      Distances come from the split-float positions (FP64 accuracy rounded
 //      to FP32).
-//   3. FP64 pass: each lane lists its candidates within h (1 + 4e-6) (FP32
-//      test with a margin) and their periodic image in shared memory, and the
-//      lists are evaluated lane-parallel in FP64 (the FP64 pipe is too narrow
-//      for lane-masked evaluation of every group candidate).  Sum w and sum
-//      m w are taken in FP64, sum q w'(q) and sum m q w'(q) in FP32 (they
-//      only scale a step below 3e-6 h).  One Newton step from the FP32 root
-//      with the derivative at that root gives h; the density at that h
-//      follows to first order from the sums at the evaluated h (neglected
-//      term ~1e-11 relative); the neighbour count at the new h is the count
-//      at the evaluated one corrected by the neighbours within 4e-6 h of it
-//      (their distances are kept, up to two; with more, or a larger step,
-//      the pass is repeated at the new h).
+//   3. Finishing pass: each lane lists its candidates within h (1 + 4e-6)
+//      (FP32 test with a margin) and their periodic image in shared memory,
+//      and the lists are evaluated lane-parallel in float-float arithmetic
+//      on the split-float positions (about 1e-11 relative in q; the FP64
+//      pipe, 1/64 of FP32 on this GPU, keeps only the sums): sum w and sum
+//      m w in FP64, sum q w'(q) and sum m q w'(q) in FP32 (they only scale a
+//      step below 3e-6 h).  One Newton step from the FP32 root with the
+//      derivative at that root gives h; the density at that h follows to
+//      first order from the sums at the evaluated h (neglected term ~1e-11
+//      relative); the neighbour count at the new h is the count at the
+//      evaluated one corrected by the neighbours within 4e-6 h of it (their
+//      distances are kept, up to two; with more, or a larger step, the pass
+//      is repeated at the new h).
 // Every loop is bounded (node-visit cap, pass caps, the stack bound); a
 // particle whose h does not converge below half the box gets NaN / -1 and
 // sets a status bit.
@@ -52,13 +53,13 @@ constexpr int kSphDeep = 64;          // above this depth a step pops a single r
 static_assert(kSphDeep + 31 + 7 * 20 + 8 <= kSphStack - kSphStackNeed, "stack bound");
 constexpr int kSphQueue = 128;        // queued leaves per warp
 constexpr int kSphQueueNeed = 32;     // a step queues at most one leaf per popped node
-constexpr int kSphList = 32;          // FP64 pass: listed candidates per lane before a flush
+constexpr int kSphList = 32;          // finishing pass: listed candidates per lane before a flush
 constexpr int kSphPass32 = 32;        // FP32 Newton passes at most
-constexpr int kSphPass64 = 8;         // FP64 passes at most
+constexpr int kSphPass64 = 8;         // finishing passes at most
 // FP32 passes stop once a Newton step on ln h is below this; the step is
 // still taken, and Newton's quadratic convergence leaves an error of about
 // (f''/2f') dl^2 ~ 1e-7 (f = ln N_eff(ln h), f' ~ 3), well inside the
-// 3e-6 h that the FP64 pass accepts in one evaluation.
+// 3e-6 h that the finishing pass accepts in one evaluation.
 constexpr float kSphConv32 = 1e-3f;
 
 struct SphArgs {
@@ -76,6 +77,42 @@ struct SphArgs {
 __device__ __forceinline__ float sph_mi1(float t) {
   const float r = __fadd_rn(__fadd_rn(t, 12582912.0f), -12582912.0f);
   return __fadd_rn(t, -r);
+}
+
+// Float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2): the
+// error-free sum and product of two floats (Knuth's two-sum; the product's
+// error from one fused multiply-add) and the products and sums built on
+// them, about 2^-46 relative.  The _rn intrinsics keep the compiler from
+// contracting or reordering the steps.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_quick(float a, float b) {  // |a| >= |b| (or a == 0)
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_mul(const FF& a, const FF& b) {
+  const FF p = ff_two_prod(a.hi, b.hi);
+  return ff_quick(p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)));
+}
+__device__ __forceinline__ FF ff_add(const FF& a, const FF& b) {
+  const FF s = ff_two_sum(a.hi, b.hi);
+  return ff_quick(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+// max(c - q, 0) for c = 1 or 1/2
+__device__ __forceinline__ FF ff_pos_diff(float c, const FF& q) {
+  const FF d = ff_two_sum(c, -q.hi);
+  const FF r = ff_quick(d.hi, __fsub_rn(d.lo, q.lo));
+  return (r.hi > 0.f) ? r : FF{0.f, 0.f};
 }
 
 struct SphBufs {
@@ -280,10 +317,10 @@ struct SphEval32 {
   }
 };
 
-// FP64 pass: candidates within hb (FP32 test with a margin) go to this lane's
-// list with their periodic image; a full list anywhere in the warp is
-// flushed, i.e. every lane evaluates its listed candidates in FP64.  Only the
-// sums that set h and rho to 1e-12 are taken in FP64 (sum w, sum m w); the
+// Finishing pass: candidates within hb (FP32 test with a margin) go to this
+// lane's list with their periodic image; a full list anywhere in the warp is
+// flushed, i.e. every lane evaluates its listed candidates in float-float and
+// adds w to FP64 sums (sum w, sum m w, which set h and rho to ~1e-12); the
 // derivatives, which scale a step below 3e-6 h, are FP32 sums of the same
 // neighbours.
 struct SphEval64 {
@@ -293,58 +330,64 @@ struct SphEval64 {
   int64_t k;           // this lane's sorted index
   float3 th, tl;
   float hb2_32;        // FP32 prefilter radius^2 (box units), with margin
-  double x[3];         // target position (physical, wrapped)
-  double ih2;          // 1 / h^2 (physical)
+  FF ih2;              // 1 / h^2 (box units)
   double S0, R0;
-  float S1, R1;        // sum q w'(q) and sum m q w'(q) at this h (the step's derivative)
+  float S1, R1;        // sum q w'(q) and sum (m / L^2) q w'(q) at this h (the step's derivative)
   double bq0, bq1;     // q = r / h of the first two neighbours in the band
   int clt, band, cnt;
   __device__ __forceinline__ void flush() {
     const TreeDev& T = A->T;
-    const double L = A->B.L;
-    const double qhi2 = (1.0 + 4e-6) * (1.0 + 4e-6), qlo = 1.0 - 4e-6;
+    const float qhi2 = (float)((1.0 + 4e-6) * (1.0 + 4e-6)), qlo = (float)(1.0 - 4e-6);
     const int top = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
     for (int t = 0; t < top; ++t) {
       if (t < cnt) {
         const int j = W->list[t][lane];
         const int code = W->img[t][lane];
-        // d = x_i - x_j - s L, s the image shift found in FP32 (one rounding,
-        // as the minimum-image definition d - L round(d / L))
-        const double s0 = (double)(code % 3 - 1), s1 = (double)((code / 3) % 3 - 1), s2 = (double)(code / 9 - 1);
-        const double d0 = fma(-s0, L, x[0] - T.x64[3 * (int64_t)j]);
-        const double d1 = fma(-s1, L, x[1] - T.x64[3 * (int64_t)j + 1]);
-        const double d2 = fma(-s2, L, x[2] - T.x64[3 * (int64_t)j + 2]);
-        const double q2 = fma(d0, d0, fma(d1, d1, d2 * d2)) * ih2;
-        if (q2 < qhi2) {
-          // q = sqrt(q2): FP32 seed and one Newton step, q0 + (q2 - q0^2) / (2 q0)
-          const float q0f = sqrtf((float)q2);
-          double q = 0.0;
-          if (q0f > 0.f) {
-            const double q0 = (double)q0f;
-            q = fma(fma(-q0, q0, q2), (double)__fdividef(0.5f, q0f), q0);
+        const float4 a = T.pA[j], b = T.pB[j];
+        // d = x_i - x_j - s (box units), s the periodic image found in the
+        // listing: the hi parts are multiples of 2^-23 in [0, 1), so their
+        // difference minus s is exact; the lo difference is rounded once
+        // (2^-48).  d = dh + dl and r^2 = |d|^2 as a float-float.
+        const float dh0 = __fsub_rn(__fsub_rn(th.x, a.x), (float)(code % 3 - 1));
+        const float dh1 = __fsub_rn(__fsub_rn(th.y, a.y), (float)((code / 3) % 3 - 1));
+        const float dh2 = __fsub_rn(__fsub_rn(th.z, a.z), (float)(code / 9 - 1));
+        const float dl0 = __fsub_rn(tl.x, b.x), dl1 = __fsub_rn(tl.y, b.y), dl2 = __fsub_rn(tl.z, b.z);
+        const FF p0 = ff_two_prod(dh0, dh0), p1 = ff_two_prod(dh1, dh1), p2 = ff_two_prod(dh2, dh2);
+        const FF s01 = ff_two_sum(p0.hi, p1.hi), s012 = ff_two_sum(s01.hi, p2.hi);
+        // the small terms: the products' errors, 2 dh dl and dl^2
+        float c = __fmaf_rn(2.0f * dh0 + dl0, dl0, __fmaf_rn(2.0f * dh1 + dl1, dl1, __fmul_rn(2.0f * dh2 + dl2, dl2)));
+        c = __fadd_rn(c, __fadd_rn(__fadd_rn(p0.lo, p1.lo), __fadd_rn(p2.lo, __fadd_rn(s01.lo, s012.lo))));
+        const FF q2 = ff_mul(ff_quick(s012.hi, c), ih2);
+        if (q2.hi < qhi2) {
+          // q = sqrt(q2): the rounded root and one correction,
+          // q0 + (q2 - q0^2) / (2 q0), with q0^2 exact
+          FF q = {0.f, 0.f};
+          const float q0 = __fsqrt_rn(q2.hi);
+          if (q0 > 0.f) {
+            const FF sq = ff_two_prod(q0, q0);
+            const float res = __fadd_rn(__fsub_rn(__fsub_rn(q2.hi, sq.hi), sq.lo), q2.lo);
+            q = ff_quick(q0, __fmul_rn(res, __fdiv_rn(0.5f, q0)));
           }
-          double w;
-          if (q <= 0.5) {
-            w = fma(q2, fma(6.0, q, -6.0), 1.0);
-          } else if (q < 1.0) {
-            const double u = 1.0 - q;
-            w = (2.0 * u) * (u * u);
-          } else {
-            w = 0.0;
-          }
-          S0 += w;
-          R0 = fma(T.m64[j], w, R0);
-          if (q < 1.0) {
-            const float qf = (float)q, uf = 1.0f - qf;
+          // w = 2 u^3 - 8 v^3, u = max(1 - q, 0), v = max(1/2 - q, 0)
+          const FF u = ff_pos_diff(1.0f, q), v = ff_pos_diff(0.5f, q);
+          const FF u3 = ff_mul(ff_mul(u, u), u), v3 = ff_mul(ff_mul(v, v), v);
+          const FF w = ff_add(FF{2.0f * u3.hi, 2.0f * u3.lo}, FF{-8.0f * v3.hi, -8.0f * v3.lo});
+          const double wd = (double)w.hi + (double)w.lo;
+          S0 += wd;
+          R0 = fma(T.m64[j], wd, R0);
+          const bool in = q.hi < 1.0f || (q.hi == 1.0f && q.lo < 0.0f);
+          if (in) {
+            const float qf = q.hi, uf = 1.0f - qf;
             const float wq = qf <= 0.5f ? qf * qf * fmaf(18.0f, qf, -12.0f) : -6.0f * qf * uf * uf;
             S1 += wq;
-            R1 = fmaf((float)T.m64[j], wq, R1);
+            R1 = fmaf(a.w, wq, R1);
           }
           if (j != (int)k) {
-            if (q < 1.0) ++clt;
-            if (q >= qlo) {
-              if (band == 0) bq0 = q;
-              else if (band == 1) bq1 = q;
+            if (in) ++clt;
+            if (q.hi >= qlo) {
+              const double qd = (double)q.hi + (double)q.lo;
+              if (band == 0) bq0 = qd;
+              else if (band == 1) bq1 = qd;
               ++band;
             }
           }
@@ -475,16 +518,13 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
     }
   }
 
-  // 3. FP64 pass(es): Newton step, density and neighbour count
+  // 3. finishing pass(es): Newton step, density and neighbour count
   const double L = A.B.L;
   bool done = !valid || fail;
   double hd = (double)h * L;
   double lo64 = 0.0, hi64 = 0.0;  // FP64 bracket (hi64 = 0: none yet)
   double h_out = NAN, rho_out = NAN;
   int ngb_out = -1;
-  double xk[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) xk[c] = T.x64[3 * kc + c];
   for (int pass = 0; pass < kSphPass64 && !st && __any_sync(0xffffffffu, !done); ++pass) {
     SphEval64 ev;
     ev.A = &A;
@@ -493,9 +533,11 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
     ev.k = k;
     ev.th = th;
     ev.tl = tl;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) ev.x[c] = xk[c];
-    ev.ih2 = 1.0 / (hd * hd);
+    {
+      const double v = (L * L) / (hd * hd);  // 1 / h^2 in box units, as a float-float
+      ev.ih2.hi = (float)v;
+      ev.ih2.lo = (float)(v - (double)ev.ih2.hi);
+    }
     const float hb = (float)(hd * (1.0 + 4e-6) / L);
     ev.hb2_32 = done ? -1.f : hb * hb * 1.0001f + 1e-14f;
     ev.S0 = ev.R0 = 0.0;
@@ -529,7 +571,7 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
         if (ev.band >= 1) c += (int)(ev.bq0 < qn) - (int)(ev.bq0 < 1.0);
         if (ev.band >= 2) c += (int)(ev.bq1 < qn) - (int)(ev.bq1 < 1.0);
         // rho at hn to first order: d(sum m w)/dh = -(sum m q w'(q)) / h
-        const double R0f = ev.R0 - (double)ev.R1 * (hn - hd) / hd;
+        const double R0f = ev.R0 - (double)ev.R1 * L * L * (hn - hd) / hd;
         h_out = hn;
         rho_out = 8.0 * R0f / (M_PI * hn * hn * hn);
         ngb_out = c;

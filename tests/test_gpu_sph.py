@@ -1,11 +1,11 @@
 """SPH density on the device against the FP64 oracle (oracle/og_sph.py).
 
 The oracle solves N_eff(h) = N_ngb by FP64 bisection to 1e-12 of h.  The
-device's grouped walk converges in FP32 (to ~1e-6) and finishes with one
-FP64 Newton step on FP64 minimum-image distances (error ~1e-11), with the
-density carried to the new h to first order (~1e-11).  So h and rho agree
-to 1e-9 relative, and neighbour counts exactly (ties at r = h have measure
-zero).
+device's grouped walk converges in FP32 (to ~1e-7) and finishes with one
+Newton step whose sums come from float-float minimum-image distances on the
+split-float positions (~1e-11 relative in q), with the density carried to
+the new h to first order (~1e-11).  So h and rho agree to 1e-9 relative,
+and neighbour counts exactly (ties at r = h have measure zero).
 """
 import numpy as np
 import pytest
