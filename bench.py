@@ -368,6 +368,37 @@ def side_workload(og, L, name, dev, theta, steps, flush):
             "timed_steps": steps, "launch": "stream launches, L2 flushed"}
 
 
+def autograd_leg(og, dev, theta, steps, flush):
+    """The adjoint configuration through torch.autograd: L = sum w . a on the
+    128^3 clustered set with seeded w; ShortRangeAccel.forward runs keys,
+    sort, tree and the forward walk, backward the adjoint walk and the
+    push-down (decisions frozen).  Stream launches, L2 flushed."""
+    import ics
+    import torch
+    w = ics.make("nfw128_adjoint")
+    pos = torch.tensor(w.pos, device=dev, requires_grad=True)
+    mass = torch.tensor(w.mass, device=dev, requires_grad=True)
+    eps = torch.tensor(w.eps, device=dev)
+    wt = torch.tensor(w.w, dtype=torch.float32, device=dev)
+
+    def run():
+        acc = og.ShortRangeAccel.apply(pos, mass, eps, w.box, w.r_s, theta)
+        return torch.autograd.grad((acc * wt).sum(), (pos, mass))
+
+    run()
+    torch.cuda.synchronize()
+    t = timed_ms(run, steps, flush)
+    k, o = og.keys_sort(pos.detach(), w.box)
+    tree = og.tree_build(k, o, pos.detach(), mass.detach(), eps, w.box)
+    _, tot, _ = og.shortrange_accel(tree, w.r_s, theta)
+    inter = int(tot.item())
+    return {"workload": f"nfw128_adjoint: {WORKLOADS['nfw128_adjoint']}", "n": w.n, "interactions_per_pass": inter,
+            "ms": t, "interactions_per_s": inter / (t * 1e-3), "particles_per_s": w.n / (t * 1e-3),
+            "timed_steps": steps,
+            "what": "ShortRangeAccel.apply + torch.autograd.grad of sum(w . a) for pos and mass: keys, sort, "
+                    "tree, forward walk; adjoint walk, push-down; stream launches, L2 flushed"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -789,6 +820,12 @@ def main():
             side[name] = {"error": f"{type(e).__name__}: {e}"}
         torch.cuda.empty_cache()
     line["other_workloads"] = side
+    if args.side:  # beside the other workloads (skipped with --side=)
+        try:
+            line["adjoint_autograd"] = autograd_leg(og, dev, args.theta, 3, flush)
+        except Exception as e:
+            line["adjoint_autograd"] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
 
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
