@@ -101,6 +101,24 @@ __device__ __forceinline__ float pm_sinc(int k, int N) {
 // loads, two products and one reciprocal.
 constexpr int kGreenMaxHalf = 513;  // N / 2 + 1 for N <= 1024
 constexpr int kGreenUnroll = 4;
+
+// i / d for i < 2^31, 0 < d and a quotient below 2^21 (here at most N^2):
+// the FP32 quotient (relative error below 3 2^-24, so off by less than one)
+// corrected on the remainder; the loops stay exact for any error.  A few
+// instructions where a 64-bit integer division takes dozens.
+__device__ __forceinline__ uint32_t div_u31(uint32_t i, uint32_t d, float inv_d) {
+  uint32_t q = (uint32_t)((float)i * inv_d);
+  int32_t r = (int32_t)(i - q * d);
+  while (r < 0) {
+    --q;
+    r += (int32_t)d;
+  }
+  while (r >= (int32_t)d) {
+    ++q;
+    r -= (int32_t)d;
+  }
+  return q;
+}
 __global__ void __launch_bounds__(256) k_pm_green(cufftComplex* __restrict__ C, int N, float inv_box,
                                                   float two_pi_over_box, float r_s) {
   __shared__ float Tk[kGreenMaxHalf];
@@ -115,20 +133,23 @@ __global__ void __launch_bounds__(256) k_pm_green(cufftComplex* __restrict__ C, 
     Tk[k] = expf(-q2 * (float)(k * k) * r_s * r_s) / (s2 * s2);
   }
   __syncthreads();
-  const int64_t total = (int64_t)N * N * H;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < total; i0 += kGreenUnroll * stride) {
+  // N <= 1024: N^2 H < 2^29, so the flat index and its split fit 32 bits
+  const uint32_t total = (uint32_t)N * (uint32_t)N * (uint32_t)H;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const float inv_H = 1.0f / (float)H, inv_N = 1.0f / (float)N;
+  for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < total; i0 += kGreenUnroll * stride) {
     cufftComplex v[kGreenUnroll];
     float g[kGreenUnroll];
 #pragma unroll
     for (int u = 0; u < kGreenUnroll; ++u) {
-      const int64_t i = i0 + u * stride;
+      const uint32_t i = i0 + u * stride;
       g[u] = 0.0f;
       if (i < total) {
         v[u] = C[i];
-        const int64_t row = i / H;
-        const int kz = (int)(i - row * H);
-        const int ix = (int)(row / N), iy = (int)(row - (int64_t)ix * N);
+        const uint32_t row = div_u31(i, (uint32_t)H, inv_H);
+        const int kz = (int)(i - row * (uint32_t)H);
+        const uint32_t ixu = div_u31(row, (uint32_t)N, inv_N);
+        const int ix = (int)ixu, iy = (int)(row - ixu * (uint32_t)N);
         const int kx = ix <= N / 2 ? ix : N - ix;  // |k|: T is even
         const int ky = iy <= N / 2 ? iy : N - iy;
         const int k2i = kx * kx + ky * ky + kz * kz;
@@ -137,7 +158,7 @@ __global__ void __launch_bounds__(256) k_pm_green(cufftComplex* __restrict__ C, 
     }
 #pragma unroll
     for (int u = 0; u < kGreenUnroll; ++u) {
-      const int64_t i = i0 + u * stride;
+      const uint32_t i = i0 + u * stride;
       if (i < total) C[i] = make_float2(v[u].x * g[u], v[u].y * g[u]);
     }
   }
