@@ -385,15 +385,23 @@ def autograd_leg(og, dev, theta, steps, flush):
         acc = og.ShortRangeAccel.apply(pos, mass, eps, w.box, w.r_s, theta)
         return torch.autograd.grad((acc * wt).sum(), (pos, mass))
 
+    def run_fused():
+        loss = og.ShortRangeLinearLoss.apply(pos, mass, eps, wt, w.box, w.r_s, theta)
+        return torch.autograd.grad(loss, (pos, mass))
+
     run()
+    run_fused()
     torch.cuda.synchronize()
     t = timed_ms(run, steps, flush)
+    tf = timed_ms(run_fused, steps, flush)
     k, o = og.keys_sort(pos.detach(), w.box)
     tree = og.tree_build(k, o, pos.detach(), mass.detach(), eps, w.box)
     _, tot, _ = og.shortrange_accel(tree, w.r_s, theta)
     inter = int(tot.item())
     return {"workload": f"nfw128_adjoint: {WORKLOADS['nfw128_adjoint']}", "n": w.n, "interactions_per_pass": inter,
             "ms": t, "interactions_per_s": inter / (t * 1e-3), "particles_per_s": w.n / (t * 1e-3),
+            "linear_loss_fused": {"ms": tf, "interactions_per_s": inter / (tf * 1e-3), "speedup": t / tf,
+                                  "what": "ShortRangeLinearLoss: the same loss and gradients from one fused walk"},
             "timed_steps": steps,
             "what": "ShortRangeAccel.apply + torch.autograd.grad of sum(w . a) for pos and mass: keys, sort, "
                     "tree, forward walk; adjoint walk, push-down; stream launches, L2 flushed"}

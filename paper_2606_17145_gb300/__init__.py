@@ -436,5 +436,34 @@ class ShortRangeAccel(torch.autograd.Function):
         return gp, gm, None, None, None, None
 
 
+class ShortRangeLinearLoss(torch.autograd.Function):
+    """L = ShortRangeLinearLoss.apply(pos, mass, eps, w, box, r_s, theta):
+    the scalar L = sum_i w_i . a_i of the short-range accelerations, for
+    weights w (float32 [n, 3]) known before the forces.
+
+    Forward: keys, sort, tree and one fused walk (og_shortrange_accel_adjoint)
+    that writes the accelerations and dL/dx, dL/dm together.  Backward scales
+    those by the incoming gradient; dL/dw = a.  The same gradients as
+    ShortRangeAccel followed by (a * w).sum(), from one walk instead of two.
+    """
+
+    @staticmethod
+    def forward(ctx, pos, mass, eps, w, box, r_s, theta):
+        keys, order = keys_sort(pos, box, check=False)
+        tree = tree_build(keys, order, pos, mass, eps, box, check=False)
+        acc, _, _, dpos, dmass = shortrange_accel_adjoint(tree, r_s, theta, w.detach().contiguous(), check=False)
+        _check(poll_status(tree.mem), "tree_build (device)")
+        ctx.save_for_backward(acc, dpos, dmass)
+        return (acc.double() * w.double()).sum()
+
+    @staticmethod
+    def backward(ctx, g):
+        acc, dpos, dmass = ctx.saved_tensors
+        gp = g * dpos if ctx.needs_input_grad[0] else None
+        gm = g * dmass if ctx.needs_input_grad[1] else None
+        gw = (g * acc).to(torch.float32) if ctx.needs_input_grad[3] else None
+        return gp, gm, None, gw, None, None, None
+
+
 def shortrange_accel_autograd(pos, mass, eps, box, r_s, theta):
     return ShortRangeAccel.apply(pos, mass, eps, box, r_s, theta)

@@ -95,3 +95,39 @@ def test_fused_argument_errors():
     ws = ws[(-ws.data_ptr()) % 256:][: need - 1]
     with pytest.raises(m.OGError):
         m.shortrange_accel_adjoint(tree, w.r_s, 0.5, wt, ws=ws)
+
+
+def test_linear_loss_autograd(orc):
+    """ShortRangeLinearLoss: L = sum w . a and, through autograd, dL/dx, dL/dm
+    and dL/dw from the fused walk, against the two-walk autograd path, the
+    oracle's gradient per particle and the oracle's accelerations."""
+    dev = device()
+    m = og()
+    w = ics.make("nfw256", 16)
+    wt = torch.tensor(ics.loss_weights(w.n, 5), dtype=torch.float32, device=dev)
+    pos = torch.tensor(w.pos, dtype=torch.float64, device=dev, requires_grad=True)
+    mass = torch.tensor(w.mass, dtype=torch.float64, device=dev, requires_grad=True)
+    eps = torch.tensor(w.eps, dtype=torch.float64, device=dev)
+    wr = wt.clone().requires_grad_(True)
+    L = m.ShortRangeLinearLoss.apply(pos, mass, eps, wr, w.box, w.r_s, 0.5)
+    # a factor 2 (exact in FP32): the two-walk path receives 2 w as its weights
+    gp, gm, gw = torch.autograd.grad(2.0 * L, (pos, mass, wr))
+    # the two-walk path
+    pos2 = pos.detach().clone().requires_grad_(True)
+    mass2 = mass.detach().clone().requires_grad_(True)
+    acc = m.ShortRangeAccel.apply(pos2, mass2, eps, w.box, w.r_s, 0.5)
+    L2 = (acc.double() * wt.double()).sum()
+    gp2, gm2 = torch.autograd.grad(2.0 * L2, (pos2, mass2))
+    assert abs(L.item() - L2.item()) <= 1e-12 * abs(L2.item())
+    assert torch.equal(gw, 2.0 * acc.detach())
+    assert (gp - gp2).abs().max().item() <= 1e-12 * gp2.abs().max().item()
+    assert (gm - gm2).abs().max().item() <= 1e-12 * gm2.abs().max().item()
+    # against the oracle
+    wd = wt.double().cpu().numpy()
+    T = orc.Tree(w.pos, w.mass, 2.8 * w.eps)
+    s = np.arange(0, w.n, 9)
+    op, om, pa, ma = T.adjoint(w.r_s, w.rcut, 0.5, wd, s, with_scale=True)
+    assert grad_scaled_err(gp.cpu().numpy()[s] / 2.0, op, pa) < GRAD_TOL
+    assert grad_scaled_err(gm.cpu().numpy()[s] / 2.0, om, ma) < GRAD_TOL
+    ao, _ = T.walk(w.r_s, w.rcut, 0.5)
+    assert err_stats(gw.double().cpu().numpy() / 2.0, ao)["rms"] <= 1e-5
