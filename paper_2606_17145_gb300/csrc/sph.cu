@@ -21,22 +21,21 @@
 //      d ln N_eff / d ln h = -sum q w'(q) / sum w(q), a bracket of the root kept
 //      from every evaluation (a step leaving it is replaced by the bracket's
 //      geometric mean) and steps clamped to a factor 2, until a step below
-//      1e-3 (taken, leaving ~1e-7).
+//      1e-2 (taken, leaving ~3e-5).
 //      Distances come from the split-float positions (FP64 accuracy rounded
 //      to FP32).
-//   3. Finishing pass: each lane lists its candidates within h (1 + 4e-6)
+//   3. Finishing pass: each lane lists its candidates within h (1 + 4e-4)
 //      (FP32 test with a margin) and their periodic image in shared memory,
 //      and the lists are evaluated lane-parallel in float-float arithmetic
 //      on the split-float positions (about 1e-11 relative in q; the FP64
 //      pipe, 1/64 of FP32 on this GPU, keeps only the sums): sum w and sum
-//      m w in FP64, sum q w'(q) and sum m q w'(q) in FP32 (they only scale a
-//      step below 3e-6 h).  One Newton step from the FP32 root with the
-//      derivative at that root gives h; the density at that h follows to
-//      first order from the sums at the evaluated h (neglected term ~1e-11
-//      relative); the neighbour count at the new h is the count at the
-//      evaluated one corrected by the neighbours within 4e-6 h of it (their
-//      distances are kept, up to two; with more, or a larger step, the pass
-//      is repeated at the new h).
+//      m w in FP64; sum q w' and sum m q w' (compensated FP32) and sum
+//      q^2 w'' and sum m q^2 w'' (FP32).  A second-order step in ln h from
+//      those sums gives h (error ~20 d^3 for a step d; steps up to 3e-4 are
+//      accepted) and the density at it; the neighbour count at the new h is
+//      the count at the evaluated one corrected by the neighbours within
+//      4e-4 h of it (their distances are kept, up to two; with more, or a
+//      larger step, the pass is repeated at the new h).
 // Every loop is bounded (node-visit cap, pass caps, the stack bound); a
 // particle whose h does not converge below half the box gets NaN / -1 and
 // sets a status bit.
@@ -58,9 +57,13 @@ constexpr int kSphPass32 = 32;        // FP32 Newton passes at most
 constexpr int kSphPass64 = 8;         // finishing passes at most
 // FP32 passes stop once a Newton step on ln h is below this; the step is
 // still taken, and Newton's quadratic convergence leaves an error of about
-// (f''/2f') dl^2 ~ 1e-7 (f = ln N_eff(ln h), f' ~ 3), well inside the
-// 3e-6 h that the finishing pass accepts in one evaluation.
-constexpr float kSphConv32 = 1e-3f;
+// (f''/2f') dl^2 ~ 3e-5 (f = ln N_eff(ln h), f' ~ 3), inside the 3e-4 step
+// that the finishing pass accepts in one evaluation.
+constexpr float kSphConv32 = 1e-2f;
+// The finishing pass lists neighbours within (1 + kSphBand) h and accepts a
+// second-order step of up to kSphStep in ln h.
+constexpr double kSphBand = 4e-4;
+constexpr double kSphStep = 3e-4;
 
 struct SphArgs {
   TreeDev T;
@@ -77,6 +80,15 @@ struct SphArgs {
 __device__ __forceinline__ float sph_mi1(float t) {
   const float r = __fadd_rn(__fadd_rn(t, 12582912.0f), -12582912.0f);
   return __fadd_rn(t, -r);
+}
+
+// Compensated (Kahan) addition: the sum is T - C.  The _rn intrinsics keep
+// the compiler from reassociating it away.
+__device__ __forceinline__ void sph_kahan_add(float& T, float& C, float x) {
+  const float y = __fsub_rn(x, C);
+  const float t = __fadd_rn(T, y);
+  C = __fsub_rn(__fsub_rn(t, T), y);
+  T = t;
 }
 
 // Float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2): the
@@ -332,12 +344,15 @@ struct SphEval64 {
   float hb2_32;        // FP32 prefilter radius^2 (box units), with margin
   FF ih2;              // 1 / h^2 (box units)
   double S0, R0;
-  float S1, R1;        // sum q w'(q) and sum (m / L^2) q w'(q) at this h (the step's derivative)
+  // the step's derivatives at this h: sum q w'(q) and sum (m / L^2) q w'(q)
+  // (FP32, compensated: C1, Q1), sum q^2 w''(q) and sum (m / L^2) q^2 w''(q)
+  float S1, R1, C1, Q1;
+  float S2, R2;
   double bq0, bq1;     // q = r / h of the first two neighbours in the band
   int clt, band, cnt;
   __device__ __forceinline__ void flush() {
     const TreeDev& T = A->T;
-    const float qhi2 = (float)((1.0 + 4e-6) * (1.0 + 4e-6)), qlo = (float)(1.0 - 4e-6);
+    const float qhi2 = (float)((1.0 + kSphBand) * (1.0 + kSphBand)), qlo = (float)(1.0 - kSphBand);
     const int top = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
     for (int t = 0; t < top; ++t) {
       if (t < cnt) {
@@ -377,10 +392,16 @@ struct SphEval64 {
           R0 = fma(T.m64[j], wd, R0);
           const bool in = q.hi < 1.0f || (q.hi == 1.0f && q.lo < 0.0f);
           if (in) {
+            // q w'(q) and q^2 w''(q): w' = 18 q^2 - 12 q, w'' = 36 q - 12 for
+            // q <= 1/2; w' = -6 u^2, w'' = 12 u (u = 1 - q) beyond
             const float qf = q.hi, uf = 1.0f - qf;
-            const float wq = qf <= 0.5f ? qf * qf * fmaf(18.0f, qf, -12.0f) : -6.0f * qf * uf * uf;
-            S1 += wq;
-            R1 = fmaf(a.w, wq, R1);
+            const bool inner = qf <= 0.5f;
+            const float wq = inner ? qf * qf * fmaf(18.0f, qf, -12.0f) : -6.0f * qf * uf * uf;
+            const float wqq = inner ? qf * qf * fmaf(36.0f, qf, -12.0f) : 12.0f * qf * qf * uf;
+            sph_kahan_add(S1, C1, wq);
+            sph_kahan_add(R1, Q1, a.w * wq);
+            S2 += wqq;
+            R2 = fmaf(a.w, wqq, R2);
           }
           if (j != (int)k) {
             if (in) ++clt;
@@ -538,10 +559,11 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
       ev.ih2.hi = (float)v;
       ev.ih2.lo = (float)(v - (double)ev.ih2.hi);
     }
-    const float hb = (float)(hd * (1.0 + 4e-6) / L);
+    const float hb = (float)(hd * (1.0 + kSphBand) / L);
     ev.hb2_32 = done ? -1.f : hb * hb * 1.0001f + 1e-14f;
     ev.S0 = ev.R0 = 0.0;
-    ev.S1 = ev.R1 = 0.f;
+    ev.S1 = ev.R1 = ev.C1 = ev.Q1 = 0.f;
+    ev.S2 = ev.R2 = 0.f;
     ev.bq0 = ev.bq1 = 0.0;
     ev.clt = ev.band = ev.cnt = 0;
     const float Rl = done ? 0.f : hb;
@@ -550,28 +572,44 @@ __global__ void __launch_bounds__(kSphWarps * 32) k_sph_density(SphArgs A) {
     if (st) break;
     ev.flush();
     if (!done) {
+      // Second-order step in d = ln(h / hd): with q' = q e^-d,
+      //   sum w(q') = S0 - d S1 + d^2 / 2 (S1 + S2) + O(d^3)
+      // (S1 = sum q w', S2 = sum q^2 w''; the spline is C^2, and neighbours
+      // entering or leaving the sphere add O(d^3)).  Solve (32/3) of it =
+      // N_ngb by Newton steps on the quadratic; its error, ~20 d^3 of N_ngb,
+      // is below 1e-9 for the accepted |d| <= kSphStep.
       const double N = (32.0 / 3.0) * ev.S0;
       if (N < A.n_ngb) lo64 = hd;
       else hi64 = hd;
-      // Newton step, dN/dh = -(32 / 3) sum q w'(q) / h taken at hd (FP32
-      // terms: the derivative only scales a step below 3e-6 h)
-      double hn;
-      if (ev.S1 < 0.f) hn = hd + (N - A.n_ngb) * hd / ((32.0 / 3.0) * (double)ev.S1);
-      else hn = N >= A.n_ngb ? 0.5 * hd : 2.0 * hd;
-      const bool small = fabs(hn - hd) <= 3e-6 * hd;
+      const double c0 = ev.S0 - (3.0 / 32.0) * A.n_ngb;
+      const double s1 = (double)ev.S1 - (double)ev.C1, r1 = (double)ev.R1 - (double)ev.Q1;
+      const double c1 = -s1, c2 = 0.5 * (s1 + (double)ev.S2);
+      double d;
+      if (c1 > 0.0) {
+        d = -c0 / c1;
+        for (int it = 0; it < 2; ++it) {
+          const double den = c1 + 2.0 * c2 * d;
+          if (den > 0.0) d -= (c0 + (c1 + c2 * d) * d) / den;
+        }
+      } else {
+        d = N >= A.n_ngb ? -0.69 : 0.69;
+      }
+      double hn = hd * exp(d);
+      const bool small = fabs(d) <= kSphStep;
       if (!small && hi64 > 0.0 && lo64 > 0.0 && !(hn > lo64 && hn < hi64)) hn = 0.5 * (lo64 + hi64);
       // with more than two band neighbours (their distances are not kept)
       // the step must be at the FP64 resolution: no neighbour then lies
       // between hd and hn short of an exact tie
-      if (small && (ev.band <= 2 || fabs(hn - hd) <= 1e-12 * hd)) {
-        // the step stays inside the band, so only band neighbours can change
-        // side between hd and hn
+      if (small && (ev.band <= 2 || fabs(d) <= 1e-12)) {
+        // the step stays inside the band (kSphBand > kSphStep), so only band
+        // neighbours can change side between hd and hn
         const double qn = hn / hd;
         int c = ev.clt;
         if (ev.band >= 1) c += (int)(ev.bq0 < qn) - (int)(ev.bq0 < 1.0);
         if (ev.band >= 2) c += (int)(ev.bq1 < qn) - (int)(ev.bq1 < 1.0);
-        // rho at hn to first order: d(sum m w)/dh = -(sum m q w'(q)) / h
-        const double R0f = ev.R0 - (double)ev.R1 * L * L * (hn - hd) / hd;
+        // rho at hn from sum m w to second order in d, as sum w above
+        const double L2 = L * L;
+        const double R0f = ev.R0 + (-d * r1 + 0.5 * d * d * (r1 + (double)ev.R2)) * L2;
         h_out = hn;
         rho_out = 8.0 * R0f / (M_PI * hn * hn * hn);
         ngb_out = c;
