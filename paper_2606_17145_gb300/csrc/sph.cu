@@ -259,18 +259,23 @@ __device__ uint32_t sph_gather(const SphArgs& A, const SphBufs& W, const SphGrou
       // and let every lane evaluate them from shared memory; a particle
       // beyond R of the box is not staged (the leaf's cube reached the
       // sphere, the particle does not)
+      // Each window of 32 slots finds its slots' leaves without a search:
+      // ecur holds the window's first slot, the leaves starting inside the
+      // window set bit (start - s0) of one OR-reduced mask (leaves hold at
+      // least one particle, so at most 31 start inside it), and slot s0 + l
+      // lies in leaf ecur + (number of starts at or before bit l).
+      int ecur = 0;
       for (int s0 = 0; s0 < run; s0 += 32) {
+        const int ek = ecur + 1 + lane;
+        const int sk = ek < nq ? W.qoff[ek] - s0 : 32;
+        const uint32_t starts = __reduce_or_sync(0xffffffffu, (sk > 0 && sk < 32) ? (1u << sk) : 0u);
         const int slot = s0 + lane;
         bool stage = false;
         float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
         int j = 0;
         if (slot < run) {
-          int lo = 0, hi = nq - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (W.qoff[mid] <= slot) lo = mid; else hi = mid - 1;
-          }
-          j = W.queue[lo].x + (slot - W.qoff[lo]);
+          const int e = ecur + __popc(starts & ((2u << lane) - 1u));
+          j = W.queue[e].x + (slot - W.qoff[e]);
           pa = T.pA[j];
           pb = T.pB[j];
           const float gx = fmaxf(fabsf(sph_mi1(pa.x - G.cx)) - G.ex, 0.f);
@@ -288,6 +293,10 @@ __device__ uint32_t sph_gather(const SphArgs& A, const SphBufs& W, const SphGrou
         __syncwarp();
         if (sm) eval(W, __popc(sm));
         __syncwarp();
+        // the leaf holding the next window's first slot
+        int en = ecur + __popc(starts);
+        if (en + 1 < nq && W.qoff[en + 1] == s0 + 32) ++en;
+        ecur = en;
       }
       nq = 0;
     } else {
