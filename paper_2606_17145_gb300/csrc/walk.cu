@@ -200,7 +200,6 @@ constexpr int kQueueNeed = 64;   // a step queues at most 2 entries per node
 constexpr int kSlots = 32;       // sources per evaluation batch
 constexpr int kRing = 2 * kSlots; // staged sources: two batches
 constexpr int kList = 512;       // (node or slot, target) list entries
-constexpr int kMap = 512;        // slots covered by the slot -> queue entry map
 
 // Stack entry: (first node | node count << 28, lane mask); node indices stay
 // below 2^28 (checked on the host).  Queue entry: (first particle or node,
@@ -212,7 +211,6 @@ struct WarpBufs {
   int4* queue;
   int* qoff;
   unsigned short* list;  // per-lane decision list (traversal) or pair list (evaluation)
-  unsigned char* emap;   // queue entry of each slot, when the queue has at most kMap slots
 };
 
 // Nodes of one traversal step that need per-lane decisions.
@@ -311,37 +309,9 @@ __device__ __forceinline__ int queue_offsets(const WalkArgs& A, const WarpBufs& 
   }
   __syncwarp();
   if (__any_sync(0xffffffffu, badq)) return -1;
-  if (run <= kMap) {
-    // slot -> entry map (entries are below kQueue <= 256)
-    for (int b0 = 0; b0 < nq; b0 += 32) {
-      const int e = b0 + lane;
-      if (e < nq) {
-        const int4 Q = W.queue[e];
-        const int c = Q.y == -1 ? 1 : Q.y;
-        const int o = W.qoff[e];
-        for (int j = 0; j < c; ++j) W.emap[o + j] = (unsigned char)e;
-      }
-    }
-    __syncwarp();
-  }
   return run;
 }
 
-
-// Queue entry holding slot s (binary search over the slot offsets).
-__device__ __forceinline__ int entry_of(const WarpBufs& W, int nq, int s) {
-  int lo = 0, hi = nq - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (W.qoff[mid] <= s) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Queue entry holding slot s (total = number of slots of the queue).
-__device__ __forceinline__ int entry_lookup(const WarpBufs& W, int nq, int total, int s) {
-  return total <= kMap ? (int)W.emap[s] : entry_of(W, nq, s);
-}
 
 // 32 x 32 bit-matrix transpose across the warp: lane r holds row r (bit c =
 // column c) and receives column r.  Five stages swap the off-diagonal blocks
@@ -559,9 +529,9 @@ struct LaneFP {
     return t;
   }
 
-  __device__ __forceinline__ Fetch fetch(const WalkArgs& A, const WarpBufs& W, int nq, int total, int s) const {
+  // Fetch slot s of queue entry e.
+  __device__ __forceinline__ Fetch fetch(const WalkArgs& A, const WarpBufs& W, int e, int s) const {
     Fetch f;
-    const int e = entry_lookup(W, nq, total, s);
     const int4 Q = W.queue[e];
     f.node = Q.y < 0;
     if (f.node) {
@@ -700,13 +670,22 @@ struct LaneFP {
     // raw slots are fetched 32 at a time and the survivors of the box test
     // are appended to the ring; pending slots occupy positions
     // [32 half, 32 half + pend) mod 64
+    // Each window of 32 slots finds its slots' entries without a search:
+    // ecur holds the window's first slot, the entries starting inside the
+    // window set bit (start - rb) of one OR-reduced mask (an entry holds at
+    // least one slot, so at most 31 start inside it), and slot rb + l lies
+    // in entry ecur + (number of starts at or before bit l).
     int pend = 0, tail = 0, half = 0;
+    int ecur = 0;
     for (int rb = 0; rb < total; rb += 32) {
+      const int ek = ecur + 1 + lane;
+      const int sk = ek < nq ? W.qoff[ek] - rb : 32;
+      const uint32_t starts = __reduce_or_sync(0xffffffffu, (sk > 0 && sk < 32) ? (1u << sk) : 0u);
       Fetch cur = {};
       bool kp = false;
       float x0 = 0.f, x1 = 0.f, x2 = 0.f;
       if (rb + lane < total) {
-        cur = fetch(A, W, nq, total, rb + lane);
+        cur = fetch(A, W, ecur + __popc(starts & ((2u << lane) - 1u)), rb + lane);
         kp = keep(A, cur, G, x0, x1, x2);
       }
       const uint32_t km = __ballot_sync(0xffffffffu, kp);
@@ -721,6 +700,10 @@ struct LaneFP {
         pend -= cnt;
         half ^= 1;
       }
+      // the entry holding the next window's first slot
+      int en = ecur + __popc(starts);
+      if (en + 1 < nq && W.qoff[en + 1] == rb + 32) ++en;
+      ecur = en;
     }
   }
 
@@ -974,7 +957,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   __shared__ int4 s_queue[kWarpsPerBlock][kQueue];
   __shared__ int s_qoff[kWarpsPerBlock][kQueue + 1];
   __shared__ unsigned short s_list[kWarpsPerBlock][kList];
-  __shared__ unsigned char s_emap[kWarpsPerBlock][kMap];
   __shared__ WarpScratch<Lane> s_scr[kWarpsPerBlock];
   __shared__ typename Lane::Smem s_lane[kWarpsPerBlock];
   __shared__ float4 s_sgb[kWarpsPerBlock][2 * kSub];
@@ -1012,7 +994,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_walk(WalkArgs A) {
   W.queue = s_queue[wib];
   W.qoff = s_qoff[wib];
   W.list = s_list[wib];
-  W.emap = s_emap[wib];
   MixedScratch& X = s_scr[wib].mix;
   typename Lane::Stage& St = s_scr[wib].stage;
   typename Lane::Smem& M = s_lane[wib];
