@@ -11,10 +11,12 @@
 //
 // Grouped walk.  One warp serves a group of 32 Hilbert-consecutive targets
 // (lane = target), as in the gravity walk.  Each pass gathers, from one
-// traversal of the tree, every leaf whose cube comes within the largest
-// lane radius of the group's bounding box (a range stack popped 32 nodes at a
-// time), and every lane evaluates the gathered particles against its own
-// radius.
+// traversal of the tree (a range stack popped 32 nodes at a time), every leaf
+// whose cube comes within R of the box of the lanes still iterating (R their
+// largest radius).  The leaves' particles are fetched 32 at a time (each
+// lane finds its slot's leaf from a start mask and a popcount), a particle
+// beyond R of that box is dropped, and every lane evaluates the staged ones
+// against its own radius.
 //   1. Start: the density of the smallest ancestor of the target's leaf that
 //      holds at least N_ngb particles gives h = (3 N_ngb / 4 pi n)^(1/3).
 //   2. FP32 passes: Newton steps on ln h, ln N_eff(h) = ln N_ngb, with
