@@ -804,8 +804,12 @@ struct LaneFP {
           const int oi = __shfl_sync(0xffffffffu, off, i);
           const int ci = __shfl_sync(0xffffffffu, c, i);
           const int first = max(oi - p0, 0);
+          // the longest run reaching back into this iteration: steps beyond
+          // it add nothing (warp-uniform, so skipping them changes no sum)
+          const int span = (int)__reduce_max_sync(0xffffffffu, (unsigned)(hv ? lane - first : 0));
 #pragma unroll
           for (int d = 1; d < 32; d <<= 1) {
+            if (d > 4 && span < d) break;
             const auto y0 = __shfl_up_sync(0xffffffffu, r.x, d);
             const auto y1 = __shfl_up_sync(0xffffffffu, r.y, d);
             const auto y2 = __shfl_up_sync(0xffffffffu, r.z, d);
