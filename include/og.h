@@ -11,6 +11,7 @@
  *   og_tree_build         octree with monopole moments, level by level
  *   og_shortrange_accel   warp-coherent Barnes-Hut walk (FP32 + Kahan, or FP64)
  *   og_shortrange_adjoint gradient of L = sum_i w_i . a_i with frozen decisions
+ *   og_shortrange_accel_adjoint  both in one walk (w known before the forces)
  *   og_pm_accel           the long-range complement on a particle mesh
  *   og_kick / og_drift    the leapfrog step's kick and drift
  *   og_sph_density        SPH density and smoothing length on the same tree
@@ -376,9 +377,11 @@ og_status og_drift(double* pos, const double* vel, int64_t n, double dt, og_stre
  *   n_ngb > 0; ws of ws_bytes >= og_sph_ws_bytes(), 256-byte aligned;
  *   outputs in the original particle order: h double[n], rho double[n],
  *   ngb int32[n] (neighbours strictly inside h, self excluded).
- *   A particle whose h cannot be bracketed below box / 2, or whose neighbour
- *   gather keeps overflowing, gets NaN / -1 and sets a status bit
+ *   A particle whose h cannot be bracketed below box / 2, or whose
+ *   iteration hits its pass caps, gets NaN / -1 and sets a status bit
  *   (og_poll_status returns OG_EWALK; a corrupt tree gives OG_ETREE).
+ *   h and rho agree with the FP64 definition to ~1e-11 relative (FP32
+ *   iterations, then a step from float-float neighbour sums).
  *   Asynchronous on the stream.
  */
 size_t og_sph_ws_bytes(void);
