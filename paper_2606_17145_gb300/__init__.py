@@ -419,8 +419,9 @@ class ShortRangeAccel(torch.autograd.Function):
     def forward(ctx, pos, mass, eps, box, r_s, theta):
         keys, order = keys_sort(pos, box, check=False)
         tree = tree_build(keys, order, pos, mass, eps, box, check=False)
-        acc, total, _ = shortrange_accel(tree, r_s, theta, check=False)
         _check(poll_status(tree.mem), "tree_build (device)")
+        # check=True: the walk's own status word is read after the call
+        acc, total, _ = shortrange_accel(tree, r_s, theta, check=True)
         ctx.tree = tree
         ctx.r_s = r_s
         ctx.theta = theta
@@ -451,8 +452,10 @@ class ShortRangeLinearLoss(torch.autograd.Function):
     def forward(ctx, pos, mass, eps, w, box, r_s, theta):
         keys, order = keys_sort(pos, box, check=False)
         tree = tree_build(keys, order, pos, mass, eps, box, check=False)
-        acc, _, _, dpos, dmass = shortrange_accel_adjoint(tree, r_s, theta, w.detach().contiguous(), check=False)
         _check(poll_status(tree.mem), "tree_build (device)")
+        # check=True: the walk's own status word (iteration cap, corrupt
+        # queue entries) is read after the call
+        acc, _, _, dpos, dmass = shortrange_accel_adjoint(tree, r_s, theta, w.detach().contiguous(), check=True)
         ctx.save_for_backward(acc, dpos, dmass)
         return (acc.double() * w.double()).sum()
 
